@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs shaped like the paper's benchmark targets.
+
+This module holds no arithmetic of the sampler: it only draws initial
+positions and target parameters with numpy's seeded generators, and states the
+closed-form second moments of each target (used to measure the bias b^2 of
+Eq. "bias" in the paper's Sec. 6).  Both the CUDA library and the FP64 oracle
+receive the same arrays from here.
+
+The paper's own targets (Inference Gym: Banana, ill-conditioned Gaussian,
+German Credit, ...) are not available offline; the workloads below stand in
+for them with the same shapes and structure:
+
+* ``gauss_d100``   diagonal Gaussian, d = 100, variances log-spaced over
+                   1e-2 .. 1e2, cold start x0 = 3 N(0, I), M = 256, 2000 steps;
+* ``banana_d100``  50 banana pairs x_a ~ N(0,1), x_b | x_a ~ N(x_a^2, 0.1^2),
+                   M = 4096, x0 ~ N(0, I), 5000 steps;
+* ``funnel_d101``  v ~ N(0, 3^2), x_i | v ~ N(0, e^v), i = 1..100, M = 4096;
+* ``logreg_d101``  Bayesian logistic regression on synthetic data X (10000 x
+                   100 standardised N(0,1) columns plus an intercept), w_true ~
+                   N(0, I/100), y ~ Bernoulli(sigmoid(X w_true)), prior N(0, I),
+                   M = 8192;
+* ``batch64``      64 diagonal Gaussians, d log-uniform in [10, 2000],
+                   condition number log-uniform in [1e2, 1e4], chains from
+                   {512, 1024, 2048, 4096}, plus one d = 10000 Gaussian with
+                   16384 chains.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG = 0, 1, 2, 3
+
+
+@dataclass
+class Problem:
+    name: str
+    kind: int
+    d: int
+    M: int
+    n_steps: int
+    x0: np.ndarray                    # [M, d] float32-representable float64
+    prec: np.ndarray | None = None    # GAUSS_DIAG precisions [d]
+    banana_sb: float = 0.1
+    funnel_sv: float = 3.0
+    X: np.ndarray | None = None       # LOGREG design [N, d]
+    y: np.ndarray | None = None       # LOGREG labels [N]
+    prior_var: float = 1.0
+    Ex2: np.ndarray | None = None     # truth E_p[x_i^2]
+    Varx2: np.ndarray | None = None   # truth Var_p[x_i^2]
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def _f32(a: np.ndarray) -> np.ndarray:
+    """Round to binary32 so that both implementations start from equal values."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def gauss_diag(d: int = 100, M: int = 256, n_steps: int = 2000, x0_scale: float = 3.0,
+               var_lo: float = 1e-2, var_hi: float = 1e2, seed: int = 0) -> Problem:
+    var = var_lo * (var_hi / var_lo) ** (np.arange(d) / max(d - 1, 1))
+    prec = _f32(1.0 / var)
+    var = 1.0 / prec
+    rng = np.random.default_rng(seed)
+    x0 = _f32(x0_scale * rng.standard_normal((M, d)))
+    return Problem("gauss_d%d" % d, GAUSS_DIAG, d, M, n_steps, x0, prec=prec,
+                   Ex2=var, Varx2=2.0 * var * var, seed=seed)
+
+
+def banana(d: int = 100, M: int = 4096, n_steps: int = 5000, sb: float = 0.1,
+           seed: int = 0) -> Problem:
+    assert d % 2 == 0
+    rng = np.random.default_rng(seed)
+    x0 = _f32(rng.standard_normal((M, d)))
+    s2 = sb * sb
+    ex2 = np.empty(d)
+    vx2 = np.empty(d)
+    ex2[0::2], vx2[0::2] = 1.0, 2.0                       # a ~ N(0,1): E a^2, Var a^2
+    eb2 = 3.0 + s2                                        # E[(a^2 + s e)^2]
+    eb4 = 105.0 + 18.0 * s2 + 3.0 * s2 * s2               # E[(a^2 + s e)^4]
+    ex2[1::2], vx2[1::2] = eb2, eb4 - eb2 * eb2
+    return Problem("banana_d%d" % d, BANANA, d, M, n_steps, x0, banana_sb=sb, Ex2=ex2,
+                   Varx2=vx2, seed=seed)
+
+
+def funnel(d: int = 101, M: int = 4096, n_steps: int = 5000, sv: float = 3.0,
+           seed: int = 0) -> Problem:
+    rng = np.random.default_rng(seed)
+    x0 = _f32(rng.standard_normal((M, d)))
+    s2 = sv * sv
+    ex2 = np.full(d, np.exp(s2 / 2.0))                    # E[e^v]
+    vx2 = np.full(d, 3.0 * np.exp(2.0 * s2) - np.exp(s2))  # 3 E[e^2v] - E[e^v]^2
+    ex2[0], vx2[0] = s2, 2.0 * s2 * s2
+    return Problem("funnel_d%d" % d, FUNNEL, d, M, n_steps, x0, funnel_sv=sv, Ex2=ex2,
+                   Varx2=vx2, seed=seed)
+
+
+def logreg(n_data: int = 10000, n_feat: int = 100, M: int = 8192, n_steps: int = 2000,
+           data_seed: int = 0, seed: int = 0) -> Problem:
+    rng = np.random.default_rng(data_seed)
+    Xf = rng.standard_normal((n_data, n_feat))
+    Xf = (Xf - Xf.mean(0)) / Xf.std(0)
+    X = np.concatenate([Xf, np.ones((n_data, 1))], axis=1)
+    d = n_feat + 1
+    w_true = rng.standard_normal(d) / np.sqrt(n_feat)
+    z = X @ w_true
+    p = 1.0 / (1.0 + np.exp(-z))
+    y = (rng.random(n_data) < p).astype(np.float64)
+    X = _f32(X)
+    rng2 = np.random.default_rng(seed)
+    x0 = _f32(rng2.standard_normal((M, d)))
+    return Problem("logreg_d%d_n%d" % (d, n_data), LOGREG, d, M, n_steps, x0, X=X, y=y,
+                   seed=seed, extra={"w_true": w_true})
+
+
+def batch64(seed: int = 0, n_small: int = 64, big_d: int = 10000, big_M: int = 16384,
+            big_kappa: float = 1e4, n_steps: int = 2000, with_big: bool = True,
+            x0_scale: float = 1.0):
+    """List of Problems: n_small Gaussians of uneven shape plus one large one."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n_small):
+        d = int(round(np.exp(rng.uniform(np.log(10), np.log(2000)))))
+        kappa = float(np.exp(rng.uniform(np.log(1e2), np.log(1e4))))
+        M = int(rng.choice([512, 1024, 2048, 4096]))
+        pr = gauss_diag(d=d, M=M, n_steps=n_steps, x0_scale=x0_scale,
+                        var_lo=kappa ** -0.5, var_hi=kappa ** 0.5, seed=seed * 1000 + k + 1)
+        pr.name = "batch%d_d%d_M%d" % (k, d, M)
+        probs.append(pr)
+    if with_big:
+        pr = gauss_diag(d=big_d, M=big_M, n_steps=n_steps, x0_scale=x0_scale,
+                        var_lo=big_kappa ** -0.5, var_hi=big_kappa ** 0.5,
+                        seed=seed * 1000 + 999)
+        pr.name = "big_d%d_M%d" % (big_d, big_M)
+        probs.append(pr)
+    return probs
+
+
+def by_name(name: str, **kw) -> Problem:
+    table = {"gauss_d100": gauss_diag, "banana_d100": banana, "funnel_d101": funnel,
+             "logreg_d101": logreg}
+    return table[name](**kw)

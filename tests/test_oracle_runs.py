@@ -1,0 +1,117 @@
+"""Whole-run pins of the oracle (Algorithm 1) against exact target moments.
+
+b^2 (Eq. "bias") of the final ensemble is compared with what M exact samples
+would give; the controller and the bisection are checked by the behaviour the
+paper describes (EEVPD tracks its target; acceptance settles at a*).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2601_16696_gb300 import workloads as W
+
+
+def _run(ora, pr, threads=0, **kw):
+    if threads:
+        ora.set_threads(threads)
+    tg = ora.OracleTarget(pr.kind, pr.d, prec=pr.prec, banana_sb=pr.banana_sb,
+                          funnel_sv=pr.funnel_sv)
+    run = ora.OracleLAPS(tg, pr.x0, seed=0, truth=(pr.Ex2, pr.Varx2),
+                         n_total_steps=pr.n_steps, **kw)
+    run.run()
+    return run
+
+
+def test_gaussian_d100_default_run(ora):
+    """The 256-chain d = 100 Gaussian, paper defaults, 2000 steps."""
+    run = _run(ora, W.gauss_diag())
+    tr = run.trace
+    first = next(r for r in tr if r["b2_avg"] < 0.01)
+    assert first["grads"] <= 400
+    assert tr[-1]["b2_avg"] < 0.01
+    # Sec. 3.1 / Fig. "GermanCredit": the measured EEVPD follows its target
+    lr = [math.log(r["eevpd"] / r["eevpd_wanted"]) for r in tr[100:]]
+    assert abs(np.median(lr)) < 0.25
+    assert run.window_T == 400
+    # with 256 chains the window statistic stays near its noise floor
+    # sqrt(2/M) ~ 0.09 > 0.01, so the literal switch rule keeps the run unadjusted
+    assert run.t_switch == -1 and tr[-1]["max_delta"] > 0.05
+
+
+def test_gaussian_forced_switch_mn2(ora):
+    run = _run(ora, W.gauss_diag(), force_switch_at=400)
+    tr = run.trace
+    adj = [r for r in tr if r["phase"] == 1]
+    assert run.t_switch == 400 and run.integrator == ora.MN2
+    assert len(adj) == (2000 - 400) // 15
+    frozen = [r for r in adj if not r["adapting"]]
+    assert frozen, "bisection never met the tolerance"
+    assert abs(np.mean([r["acc"] for r in frozen]) - 0.7) < 0.06
+    assert tr[-1]["b2_avg"] < 0.01
+    assert tr[-1]["grads"] == 1 + 400 + len(adj) * 15 * 2
+    # sigma of the preconditioner is the ensemble std at the switch
+    sig = run.sigma()
+    assert np.all(sig > 0)
+    np.testing.assert_allclose(np.log(sig ** 2), np.log(W.gauss_diag().Ex2), atol=0.5)
+
+
+def test_banana_forced_switch(ora):
+    pr = W.banana(d=10, M=1024, n_steps=2000)
+    run = _run(ora, pr, force_switch_at=400)
+    assert run.trace[-1]["b2_max"] < 0.02
+    assert any(r["b2_max"] < 0.01 for r in run.trace)
+
+
+def test_gaussian_mn4_above_200_dims(ora):
+    pr = W.gauss_diag(d=250, M=256, n_steps=1500, var_lo=0.1, var_hi=10.0, x0_scale=1.0)
+    run = _run(ora, pr, force_switch_at=600)
+    assert run.integrator == ora.MN4
+    adj = [r for r in run.trace if r["phase"] == 1]
+    frozen = [r for r in adj if not r["adapting"]]
+    assert frozen and abs(np.mean([r["acc"] for r in frozen]) - 0.9) < 0.06
+    assert run.trace[-1]["b2_avg"] < 0.01
+    assert adj[-1]["grads"] - adj[-2]["grads"] == 15 * 5
+
+
+def test_funnel_small(ora):
+    pr = W.funnel(d=11, M=1024, n_steps=2000)
+    run = _run(ora, pr, force_switch_at=400)
+    assert run.trace[-1]["b2_max"] < 0.05
+
+
+def test_thread_count_does_not_change_results(ora):
+    pr = W.gauss_diag(d=20, M=64, n_steps=400)
+    a = _run(ora, pr, threads=1, force_switch_at=100)
+    b = _run(ora, pr, threads=4, force_switch_at=100)
+    ora.set_threads(0)
+    np.testing.assert_array_equal(a.x(), b.x())
+    assert [r["eps"] for r in a.trace] == [r["eps"] for r in b.trace]
+
+
+def test_nonfinite_chains_are_reverted(ora):
+    """A step that overflows (cosh of a huge delta) leaves every chain where
+    it was and halves the step size."""
+    pr = W.gauss_diag(d=10, M=8, n_steps=100)
+    tg = ora.OracleTarget(pr.kind, pr.d, prec=pr.prec)
+    run = ora.OracleLAPS(tg, pr.x0, seed=0, eps0_coef=1e9)
+    eps0 = run.trace[0]["eps"]
+    y0, u0, g0, lp0 = run.state()
+    run.iterate(1)
+    r = run.trace[1]
+    assert r["nonfinite"] == 8
+    assert r["eps"] == pytest.approx(eps0 / 2)
+    y1, u1, g1, lp1 = run.state()
+    np.testing.assert_array_equal(y1, y0)
+    np.testing.assert_array_equal(u1, u0)
+    np.testing.assert_array_equal(lp1, lp0)
+
+
+def test_step_count_and_stop(ora):
+    """A run stops at n_total steps: T = ceil(0.2 n) window, proposals of N."""
+    pr = W.gauss_diag(d=12, M=32, n_steps=107)
+    run = _run(ora, pr, force_switch_at=30)
+    adj = [r for r in run.trace if r["phase"] == 1]
+    assert len(adj) == (107 - 30) // 15
+    assert run.t == 30 + 15 * len(adj) <= 107
+    assert run.window_T == 22
