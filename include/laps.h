@@ -1,0 +1,230 @@
+/*
+ * laps.h -- C ABI of the GB300 (sm_103a) LAPS library, liblaps.so.
+ *
+ * LAPS (Late Adjusted Parallel Sampler; Robnik & Seljak, "Faster parallel
+ * MCMC: Metropolis adjustment is best served warm") advances an ensemble of M
+ * chains of a d-dimensional target: first by unadjusted microcanonical
+ * Langevin (MCLMC) steps whose step size follows the ensemble's bias estimate
+ * (Sec. 3), then, after the switch rule of Sec. 4 and a diagonal
+ * preconditioner, by Metropolis-adjusted proposals (MAMS, App. F) whose step
+ * size is bisected to a target acceptance (Sec. 5).  Algorithm 1 (App. C)
+ * states the loop this library runs.  Per the paper's statement of the
+ * problem (Sec. 1 "Our contributions", Alg. 1 input) the user supplies the
+ * target log-density with its gradient and the initial positions.
+ *
+ * Conventions (every entry point):
+ *  - Return laps_status; nothing throws across the ABI.  laps_last_error()
+ *    gives a thread-local message for the last failing call.
+ *  - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them.  "host" pointers are plain host memory.
+ *  - Arrays are row-major, chain-major and contiguous: x[m*d + i] is
+ *    coordinate i of chain m, FP32.  A device pointer that is not 4-byte
+ *    aligned returns LAPS_ERR_INVALID_ARG.
+ *  - All GPU work is ordered on the cudaStream_t argument (pass it as a
+ *    void*; NULL is the legacy default stream).  Only laps_get_stats,
+ *    laps_get_trace, laps_checkpoint and laps_restore synchronise.
+ *  - Errors raised inside a kernel (a bounded wait that expired, a bad
+ *    parameter) are latched in a device status word and returned by the next
+ *    call that reads it (laps_get_stats, or any synchronising call).
+ *  - A laps_ctx is not thread-safe; different contexts are independent.
+ */
+#ifndef LAPS_H
+#define LAPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAPS_OK = 0,
+    LAPS_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or config value */
+    LAPS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
+    LAPS_ERR_OOM = 3,           /* device allocation failed */
+    LAPS_ERR_TIMEOUT = 4,       /* a bounded device-side wait (grid barrier) expired */
+    LAPS_ERR_NONFINITE = 5,     /* every chain produced non-finite values */
+    LAPS_ERR_UNSUPPORTED = 6    /* shape/target combination not built */
+} laps_status;
+
+/* Targets with hand-written log-density and gradient kernels. */
+typedef enum {
+    LAPS_GAUSS_DIAG = 0,  /* log p = -1/2 sum_i prec_i x_i^2 */
+    LAPS_BANANA = 1,      /* pairs (a,b) = (x_2k, x_2k+1): a ~ N(0,1), b|a ~ N(a^2, sb^2); d even */
+    LAPS_FUNNEL = 2,      /* v = x_0 ~ N(0, sv^2), x_i|v ~ N(0, e^v), i = 1..d-1 */
+    LAPS_LOGREG = 3       /* sum_n [y_n z_n - softplus(z_n)] - |w|^2/(2 prior_var), z = X w */
+} laps_target_kind;
+
+/* Arithmetic of the logistic-regression contraction in the unadjusted phase. */
+typedef enum {
+    LAPS_FP32 = 0,   /* FP32 everywhere */
+    LAPS_MIXED = 1   /* BF16 tensor-core contraction (FP32 accumulate) while unadjusted */
+} laps_precision;
+
+typedef struct {
+    laps_target_kind kind;
+    int64_t d;              /* dimension, >= 2 */
+    const float* prec;      /* GAUSS_DIAG: device [d] precisions 1/sigma_i^2 */
+    double banana_sb;       /* BANANA: conditional std of x_b (0.1) */
+    double funnel_sv;       /* FUNNEL: std of v (3) */
+    int64_t n_data;         /* LOGREG: rows of X */
+    const float* X;         /* LOGREG: device [n_data][d] design matrix (intercept included) */
+    const float* y;         /* LOGREG: device [n_data] labels in {0, 1} */
+    double prior_var;       /* LOGREG: prior variance of each weight (1) */
+} laps_target_desc;
+
+typedef struct laps_target laps_target;
+typedef struct laps_ctx laps_ctx;
+
+/* Algorithm settings; laps_config_default fills the paper's values. */
+typedef struct {
+    double C;                /* asymptotic / total bias ratio, 0.025 (Sec. 3.1) */
+    double alpha;            /* L = alpha sqrt(sum_i Var x_i), 2 (Eq. "L") */
+    double switch_tol;       /* switch when max_i delta[x_i^2] < tol, 0.01 (Sec. 4) */
+    double window_frac;      /* window T = ceil(window_frac * n_total_steps), 0.2 (Sec. 4) */
+    double acc_tol;          /* stop bisecting once |a - a*| <= acc_tol, 0.03 (Sec. 5.1) */
+    double adj_L_factor;     /* adjusted L = adj_L_factor * N * eps, 1.25 (Sec. 5.2) */
+    double eps0_coef;        /* eps0 = eps0_coef * sqrt(d), 0.01 (Alg. 1) */
+    double a_target_mn2;     /* target acceptance with MN2, 0.7 (Sec. 5.1) */
+    double a_target_mn4;     /* target acceptance with MN4, 0.9 (Sec. 5.1) */
+    int n_total_steps;       /* maxiter in integrator steps (Alg. 1) */
+    int steps_per_proposal;  /* N = 15 (Sec. 5.2) */
+    int mn4_min_dim;         /* MN4 when d > mn4_min_dim, 200 (App. E) */
+    int eevpd_centered;      /* 1: EEVPD = Var[Delta]/d (Eq. EEVPD); 0: mean Delta^2/d (Alg. 1) */
+    int adjusted;            /* 0: never switch (unadjusted only) */
+    int force_switch_at;     /* > 0: switch after exactly this many unadjusted steps */
+    double stop_b2;          /* > 0 (needs laps_set_truth): finish once b^2 < stop_b2 */
+    int stop_b2_max;         /* 0: use b^2_avg for stop_b2; 1: use b^2_max */
+    laps_precision precision;
+    int64_t barrier_timeout_ns;  /* bound of every device-side wait; default 2e9 */
+    int chains_per_block;    /* 0: chosen by the library; else chains per thread block */
+    int lanes_per_chain;     /* 0: chosen; else 4, 8, 16 or 32 lanes hold one chain */
+    int coords_per_lane;     /* 0: chosen; else 4, 8 or 16 coordinates per lane */
+    int barrier_extra_arrivals;  /* test hook, 0 in use: every grid barrier also waits for
+                                    this many arrivals that never come, so its bounded wait
+                                    expires and the launch ends with LAPS_ERR_TIMEOUT */
+} laps_config;
+
+/* Snapshot of the sampler (laps_get_stats). */
+typedef struct {
+    int phase;               /* 0 unadjusted, 1 adjusted */
+    int t;                   /* integrator steps taken */
+    int t_switch;            /* step of the switch, -1 before */
+    int integrator;          /* 0 LF, 1 MN2, 2 MN4 */
+    int adapting;            /* adjusted phase: bisection still active */
+    int done;                /* the run reached n_total_steps or stop_b2 */
+    int iterations;          /* Alg. 1 loop iterations run (steps or proposals) */
+    int nonfinite_total;     /* chain updates reverted/rejected for non-finite values */
+    long long grads;         /* gradient evaluations per chain so far (init included) */
+    double eps, L;           /* hyperparameters of the next iteration */
+    double eevpd, eevpd_wanted, dtilde, max_delta; /* last unadjusted iteration */
+    double acc;              /* last adjusted iteration: mean acceptance probability */
+    double b2_max, b2_avg;   /* current second-moment bias (NaN without truth) */
+    double sum_var;          /* sum_i Var[x_i] of the current ensemble */
+    int b2_first_t;          /* first t with b^2 (stop kind) < 0.01, -1 if never */
+    long long b2_first_grads;
+    double b2_first_ns;      /* device time from the start of laps_init to that row */
+} laps_stats;
+
+/* One row per Alg. 1 iteration; row 0 describes the initial ensemble. */
+typedef struct {
+    int phase, t;
+    double eps, L, eps_used, eevpd, eevpd_wanted, dtilde, max_delta, acc;
+    double b2_max, b2_avg, sum_var;
+    int nonfinite, adapting;
+    long long grads;
+    double time_ns;          /* device %globaltimer relative to laps_init */
+} laps_trace_row;
+
+void laps_config_default(laps_config* cfg);
+const char* laps_last_error(void);
+const char* laps_version(void);
+
+/* ---- targets ------------------------------------------------------------
+ * laps_target_create copies the descriptor (the device arrays it points to
+ * must outlive the target; LOGREG keeps BF16/FP32 copies of X it owns). */
+laps_status laps_target_create(const laps_target_desc* desc, laps_target** out);
+void laps_target_destroy(laps_target* tg);
+
+/* log p and grad log p of M points: x device [M][d], logp device [M],
+ * grad device [M][d].  Forward and hand-written backward of the target (the
+ * kernels the sampler uses), FP32 in and out with compensated sums. */
+laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
+                                  float* logp, float* grad, void* stream);
+
+/* ---- one sampling problem ---------------------------------------------- */
+/* Allocates the ensemble state (x, u, g, log p in the sampler's layout), the
+ * reduction scratch, the moving window of Sec. 4 and the trace.  The target
+ * must outlive the context. */
+laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg,
+                        laps_ctx** out);
+void laps_destroy(laps_ctx* ctx);
+
+/* Alg. 1 initialisation: x0 device [M][d] (copied), or NULL to draw
+ * x0 = x0_scale * N(0, I) from the Philox stream (tag 0) of `seed`; then
+ * g0, log p0, u0 = g0/|g0|, eps0 = eps0_coef sqrt(d), L0 = Eq. "L". */
+laps_status laps_init(laps_ctx* ctx, const float* x0, double x0_scale, uint64_t seed,
+                      void* stream);
+
+/* Runs up to n_iters iterations of Alg. 1 (an unadjusted step, or one MAMS
+ * proposal of N steps), fewer if the run finishes.  One cooperative launch. */
+laps_status laps_step(laps_ctx* ctx, int n_iters, void* stream);
+
+/* Runs to the end (n_total_steps, or stop_b2). */
+laps_status laps_run(laps_ctx* ctx, void* stream);
+
+/* Freezes (frozen = 1) or re-enables the adjusted-phase bisection. */
+laps_status laps_adapt_freeze(laps_ctx* ctx, int frozen);
+
+/* Chain positions in the target's coordinates (x = sigma o y after the
+ * switch): x_out device [M][d]. */
+laps_status laps_sample(const laps_ctx* ctx, float* x_out, void* stream);
+
+/* Raw sampler state in sampler coordinates: y, u, grad_y device [M][d] and
+ * logp device [M] (double); sigma device [d] (1 before the switch).  Any
+ * pointer may be NULL. */
+laps_status laps_get_state(const laps_ctx* ctx, float* y, float* u, float* g, double* logp,
+                           float* sigma, void* stream);
+
+/* Truth for b^2 (Eq. "bias"): Ex2, Varx2 host [d] = E_p[x_i^2], Var_p[x_i^2]. */
+laps_status laps_set_truth(laps_ctx* ctx, const double* Ex2, const double* Varx2);
+
+/* Synchronises the stream of the last launch, then reports. */
+laps_status laps_get_stats(laps_ctx* ctx, laps_stats* out);
+/* Copies up to cap rows (row 0 = initial ensemble); *n = rows available. */
+laps_status laps_get_trace(laps_ctx* ctx, laps_trace_row* rows, int cap, int* n);
+
+/* Checkpoint of everything the run depends on (state, hyperparameters,
+ * window, preconditioner, trace, seed).  host_blob NULL: *size = bytes
+ * needed.  Restoring into a context created with the same target, M and
+ * config continues bit-exactly (the random stream is a function of t). */
+laps_status laps_checkpoint(laps_ctx* ctx, void* host_blob, size_t* size);
+laps_status laps_restore(laps_ctx* ctx, const void* host_blob, size_t size);
+
+/* ---- the random stream --------------------------------------------------
+ * Philox4x32-10 (Salmon et al., SC'11): ctr device [n][4] counters, key =
+ * (seed low word, seed high word), out device [n][4].  The sampler draws with
+ * counter (coordinate block j, chain m, step t, tag | pid << 8); tags: 0
+ * initial positions, 1 first O map of a step, 2 second O map, 3 full velocity
+ * refresh of a MAMS proposal (t = proposal index), 4 Metropolis uniform
+ * (j = 0, t = proposal index). */
+laps_status laps_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
+                        void* stream);
+/* The sampler's standard normals: out device [nm][d] for chains m0..m0+nm-1
+ * under (t, tag, pid); coordinate i uses block i/4, Box-Muller pair (i%4)/2,
+ * uniforms ((r >> 9) + 1/2) 2^-23. */
+laps_status laps_normals(uint64_t seed, uint32_t m0, int64_t nm, uint32_t t, uint32_t tag,
+                         uint32_t pid, int64_t d, float* out, void* stream);
+
+/* Launch shape the context uses (for tests and the autotuner). */
+typedef struct {
+    int chains_per_block, lanes_per_chain, coords_per_lane, threads, blocks;
+    int resident;            /* 1: register-resident persistent kernel */
+} laps_launch_info;
+laps_status laps_get_launch_info(const laps_ctx* ctx, laps_launch_info* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

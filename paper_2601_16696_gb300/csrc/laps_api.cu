@@ -1,0 +1,593 @@
+// laps_api.cu -- host side of the C ABI declared in include/laps.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "laps_internal.h"
+
+namespace laps {
+const void* resident_kernel_0(int lpc, int cpl);
+const void* resident_kernel_1(int lpc, int cpl);
+const void* resident_kernel_2(int lpc, int cpl);
+
+static thread_local std::string g_err;
+
+laps_status fail(laps_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+laps_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LAPS_ERR_OOM : LAPS_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+static const void* resident_fn(int kind, int lpc, int cpl) {
+    switch (kind) {
+    case TGT_GAUSS: return resident_kernel_0(lpc, cpl);
+    case TGT_BANANA: return resident_kernel_1(lpc, cpl);
+    case TGT_FUNNEL: return resident_kernel_2(lpc, cpl);
+    }
+    return nullptr;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ------------------------------------------------------------------ small kernels
+__global__ void pack_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t M,
+                                 int d, int d_pad) {
+    const int64_t n = M * (int64_t)d_pad;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / d_pad;
+        const int i = (int)(k - m * d_pad);
+        dst[k] = i < d ? src[m * d + i] : 0.0f;
+    }
+}
+__global__ void unpack_rows_kernel(const float* __restrict__ src, const float* __restrict__ scale,
+                                   float* __restrict__ dst, int64_t M, int d, int d_pad) {
+    const int64_t n = M * (int64_t)d;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / d;
+        const int i = (int)(k - m * d);
+        dst[k] = (scale ? scale[i] : 1.0f) * src[m * d_pad + i];
+    }
+}
+__global__ void fill_kernel(float* p, float v, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        p[k] = v;
+}
+
+static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+static void coefs_table(Coefs& cf) {
+    std::memset(&cf, 0, sizeof(cf));
+    // LF: B_{eps/2} A_eps B_{eps/2}
+    cf.K[INTEG_LF] = 2;
+    cf.b[INTEG_LF][0] = 0.5f; cf.b[INTEG_LF][1] = 0.5f;
+    cf.a[INTEG_LF][0] = 1.0f;
+    // MN2 (Omelyan minimal norm, second order): b1, 1/2, b2 = 1 - 2 b1, 1/2, b1
+    const double m2b1 = 0.1931833275;
+    cf.K[INTEG_MN2] = 3;
+    cf.b[INTEG_MN2][0] = (float)m2b1; cf.b[INTEG_MN2][1] = (float)(1.0 - 2.0 * m2b1);
+    cf.b[INTEG_MN2][2] = (float)m2b1;
+    cf.a[INTEG_MN2][0] = 0.5f; cf.a[INTEG_MN2][1] = 0.5f;
+    // MN4: b1 a1 b2 a2 b3 a3 b3 a2 b2 a1 b1; b3 and a3 from sum b = sum a = 1
+    const double b1 = 0.0839831526, b2 = 0.6822365335, a1 = 0.2539785108, a2 = -0.032302867;
+    const double b3 = 0.5 - b1 - b2, a3 = 1.0 - 2.0 * (a1 + a2);
+    const double bb[6] = {b1, b2, b3, b3, b2, b1}, aa[5] = {a1, a2, a3, a2, a1};
+    cf.K[INTEG_MN4] = 6;
+    for (int k = 0; k < 6; ++k) cf.b[INTEG_MN4][k] = (float)bb[k];
+    for (int k = 0; k < 5; ++k) cf.a[INTEG_MN4][k] = (float)aa[k];
+}
+
+// ------------------------------------------------------------------ launch shape
+static const int kShapes[][2] = {{4, 4}, {8, 4}, {8, 8}, {16, 4}, {16, 8}, {32, 4}, {32, 8}, {32, 16}};
+
+static size_t resident_smem(int d_pad, int threads, int lpc, int d, int G) {
+    const int nwarps = threads / 32, slots = threads / lpc;
+    const int slice = (d + G - 1) / G + 1;
+    return (size_t)nwarps * d_pad * sizeof(float) + (size_t)slots * NCS * sizeof(double) +
+           (size_t)slice * NSL * sizeof(double);
+}
+
+laps_status choose_shape(laps_ctx* c) {
+    int dev;
+    CK(cudaGetDevice(&dev));
+    int nsm;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int kind = c->tg->kind;
+    struct Cand { int lpc, cpl, threads, G; size_t smem; double score; };
+    std::vector<Cand> ok;
+    for (auto& sh : kShapes) {
+        const int lpc = sh[0], cpl = sh[1];
+        if (lpc * cpl < c->d_pad) continue;
+        if (c->cfg.lanes_per_chain && lpc != c->cfg.lanes_per_chain) continue;
+        if (c->cfg.coords_per_lane && cpl != c->cfg.coords_per_lane) continue;
+        const void* fn = resident_fn(kind, lpc, cpl);
+        if (!fn) continue;
+        std::vector<int> tlist;
+        if (c->cfg.chains_per_block > 0) tlist.push_back(c->cfg.chains_per_block * lpc);
+        else tlist = {128, 256, 512};
+        for (int threads : tlist) {
+            if (threads < 32 || threads > kMaxThreads || threads % 32) continue;
+            const int cpb = threads / lpc;
+            const int G = (int)((c->M + cpb - 1) / cpb);
+            const size_t smem = resident_smem(c->d_pad, threads, lpc, c->d, G);
+            if (smem > 200 * 1024) continue;
+            CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int bps = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem));
+            if ((long long)bps * nsm < G) continue;
+            // prefer the smallest per-lane footprint that keeps every chain resident,
+            // then more chains per block (fewer blocks in the barrier)
+            const double score = cpl * 1000.0 + (double)G / 1000.0;
+            ok.push_back({lpc, cpl, threads, G, smem, score});
+        }
+    }
+    if (ok.empty())
+        return fail(LAPS_ERR_UNSUPPORTED,
+                    "no register-resident launch shape holds M=" + std::to_string(c->M) +
+                        " chains of d=" + std::to_string(c->d) + " co-resident on this GPU");
+    auto best = *std::min_element(ok.begin(), ok.end(),
+                                  [](const Cand& a, const Cand& b) { return a.score < b.score; });
+    c->lpc = best.lpc;
+    c->cpl = best.cpl;
+    c->threads = best.threads;
+    c->G = best.G;
+    c->smem = best.smem;
+    c->fn = resident_fn(kind, best.lpc, best.cpl);
+    return LAPS_OK;
+}
+
+// ------------------------------------------------------------------ launch
+laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
+                            cudaStream_t st) {
+    KParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.M = (int)c->M;
+    P.d = c->d;
+    P.d_pad = c->d_pad;
+    P.nblk = c->d_pad / 4;
+    P.kind = c->tg->kind;
+    P.inv_s2 = (float)(1.0 / (c->tg->desc.banana_sb * c->tg->desc.banana_sb));
+    P.inv_sv2 = (float)(1.0 / (c->tg->desc.funnel_sv * c->tg->desc.funnel_sv));
+    P.prec = c->tg->prec_pad;
+    P.y = c->y;
+    P.u = c->u;
+    P.g = c->g;
+    P.logp = c->logp;
+    P.sigma = c->sigma;
+    P.x0 = x0;
+    P.x0_scale = x0_scale;
+    P.part_coord = c->part_coord;
+    P.part_chain = c->part_chain;
+    P.part_slice = c->part_slice;
+    P.var_y = c->var_y;
+    P.win = c->win;
+    P.win_s1 = c->win_s1;
+    P.win_s2 = c->win_s2;
+    P.Ex2 = c->have_truth ? c->Ex2 : nullptr;
+    P.Varx2 = c->have_truth ? c->Varx2 : nullptr;
+    P.hyper = c->hyper;
+    P.trace = c->trace;
+    P.trace_cap = c->trace_cap;
+    P.bar_count = c->bar;
+    P.bar_gen = c->bar + 1;
+    P.status = c->status;
+    const laps_config& g = c->cfg;
+    P.C = g.C;
+    P.alpha = g.alpha;
+    P.switch_tol = g.switch_tol;
+    P.acc_tol = g.acc_tol;
+    P.adj_L_factor = g.adj_L_factor;
+    P.eps0 = g.eps0_coef * std::sqrt((double)c->d);
+    P.a_target_mn2 = g.a_target_mn2;
+    P.a_target_mn4 = g.a_target_mn4;
+    P.stop_b2 = g.stop_b2;
+    P.stop_b2_max = g.stop_b2_max;
+    P.T = c->T;
+    P.n_total = g.n_total_steps;
+    P.N = g.steps_per_proposal;
+    P.mn4_min_dim = g.mn4_min_dim;
+    P.eevpd_centered = g.eevpd_centered;
+    P.adjusted = g.adjusted;
+    P.force_switch_at = g.force_switch_at;
+    P.timeout_ns = g.barrier_timeout_ns;
+    P.seed_lo = (uint32_t)c->seed;
+    P.seed_hi = (uint32_t)(c->seed >> 32);
+    P.pid = 0;
+    P.mode = mode;
+    P.n_iters = n_iters;
+    P.G = c->G;
+    P.bar_extra = g.barrier_extra_arrivals;
+
+    CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
+    const Coefs* cf = c->coefs;
+    void* args[] = {&P, &cf};
+    CK(cudaLaunchCooperativeKernel(c->fn, dim3(c->G), dim3(c->threads), args, c->smem, st));
+    c->last_stream = st;
+    return LAPS_OK;
+}
+
+}  // namespace laps
+
+using namespace laps;
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* laps_last_error(void) { return g_err.c_str(); }
+const char* laps_version(void) { return "laps-gb300 0.1 (sm_103a)"; }
+
+void laps_config_default(laps_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->C = 0.025;
+    c->alpha = 2.0;
+    c->switch_tol = 0.01;
+    c->window_frac = 0.2;
+    c->acc_tol = 0.03;
+    c->adj_L_factor = 1.25;
+    c->eps0_coef = 0.01;
+    c->a_target_mn2 = 0.7;
+    c->a_target_mn4 = 0.9;
+    c->n_total_steps = 2000;
+    c->steps_per_proposal = 15;
+    c->mn4_min_dim = 200;
+    c->eevpd_centered = 1;
+    c->adjusted = 1;
+    c->force_switch_at = 0;
+    c->stop_b2 = 0.0;
+    c->stop_b2_max = 0;
+    c->precision = LAPS_FP32;
+    c->barrier_timeout_ns = 2000000000LL;
+    c->chains_per_block = 0;
+    c->lanes_per_chain = 0;
+    c->coords_per_lane = 0;
+}
+
+laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) {
+    if (!desc || !out) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    const int64_t d = desc->d;
+    if (d < 2 || d > (1 << 24)) return fail(LAPS_ERR_INVALID_ARG, "d must be in [2, 2^24]");
+    switch (desc->kind) {
+    case LAPS_GAUSS_DIAG:
+        if (!desc->prec || !aligned(desc->prec, 4))
+            return fail(LAPS_ERR_INVALID_ARG, "GAUSS_DIAG needs a device prec[d]");
+        break;
+    case LAPS_BANANA:
+        if (d % 2) return fail(LAPS_ERR_INVALID_ARG, "BANANA needs an even d");
+        if (!(desc->banana_sb > 0)) return fail(LAPS_ERR_INVALID_ARG, "banana_sb must be > 0");
+        break;
+    case LAPS_FUNNEL:
+        if (!(desc->funnel_sv > 0)) return fail(LAPS_ERR_INVALID_ARG, "funnel_sv must be > 0");
+        break;
+    case LAPS_LOGREG:
+        return fail(LAPS_ERR_UNSUPPORTED, "LOGREG is served by the logreg entry points");
+    default:
+        return fail(LAPS_ERR_INVALID_ARG, "unknown target kind");
+    }
+    laps_target* t = new laps_target();
+    t->desc = *desc;
+    t->kind = (int)desc->kind;
+    t->d = (int)d;
+    t->d_pad = (int)((d + 3) / 4 * 4);
+    if (desc->kind == LAPS_GAUSS_DIAG) {
+        cudaError_t e = cudaMalloc(&t->prec_pad, t->d_pad * sizeof(float));
+        if (e != cudaSuccess) { delete t; return cuda_fail(e, "cudaMalloc prec"); }
+        cudaMemset(t->prec_pad, 0, t->d_pad * sizeof(float));
+        e = cudaMemcpy(t->prec_pad, desc->prec, d * sizeof(float), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) { cudaFree(t->prec_pad); delete t; return cuda_fail(e, "copy prec"); }
+    }
+    *out = t;
+    return LAPS_OK;
+}
+
+void laps_target_destroy(laps_target* t) {
+    if (!t) return;
+    if (t->prec_pad) cudaFree(t->prec_pad);
+    delete t;
+}
+
+laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg, laps_ctx** out) {
+    if (!tg || !cfg || !out) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (M < 2 || M > (1LL << 30)) return fail(LAPS_ERR_INVALID_ARG, "M must be in [2, 2^30]");
+    if (cfg->n_total_steps < 1 || cfg->steps_per_proposal < 1 || !(cfg->window_frac > 0) ||
+        !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0)
+        return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
+    laps_ctx* c = new laps_ctx();
+    c->tg = tg;
+    c->M = M;
+    c->cfg = *cfg;
+    c->d = tg->d;
+    c->d_pad = tg->d_pad;
+    c->T = std::max(2, (int)std::ceil(cfg->window_frac * (double)cfg->n_total_steps));
+    c->trace_cap = cfg->n_total_steps + 2;
+    laps_status st = choose_shape(c);
+    if (st != LAPS_OK) { delete c; return st; }
+    const size_t Md = (size_t)M * c->d_pad;
+    auto alloc = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        c->allocs.push_back(*p);
+        return true;
+    };
+    bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
+              alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp, M * 8) &&
+              alloc((void**)&c->sigma, c->d_pad * 4) &&
+              alloc((void**)&c->part_coord, (size_t)NQ * c->d_pad * c->G * 8) &&
+              alloc((void**)&c->part_chain, (size_t)NCS * c->G * 8) &&
+              alloc((void**)&c->part_slice, (size_t)NSL * c->G * 8) &&
+              alloc((void**)&c->var_y, c->d_pad * 8) &&
+              alloc((void**)&c->win, (size_t)c->T * c->d_pad * 8) &&
+              alloc((void**)&c->win_s1, c->d_pad * 8) && alloc((void**)&c->win_s2, c->d_pad * 8) &&
+              alloc((void**)&c->Ex2, c->d_pad * 8) && alloc((void**)&c->Varx2, c->d_pad * 8) &&
+              alloc((void**)&c->hyper, sizeof(Hyper)) &&
+              alloc((void**)&c->trace, (size_t)c->trace_cap * sizeof(laps_trace_row)) &&
+              alloc((void**)&c->bar, 4 * sizeof(unsigned)) && alloc((void**)&c->status, sizeof(int)) &&
+              alloc((void**)&c->coefs, sizeof(Coefs));
+    if (!ok) {
+        laps_destroy(c);
+        return fail(LAPS_ERR_OOM, "device allocation of the ensemble state failed");
+    }
+    Coefs cf;
+    coefs_table(cf);
+    cudaMemcpy(c->coefs, &cf, sizeof(cf), cudaMemcpyHostToDevice);
+    cudaMemset(c->status, 0, sizeof(int));
+    cudaMemset(c->y, 0, Md * 4);
+    cudaMemset(c->u, 0, Md * 4);
+    cudaMemset(c->g, 0, Md * 4);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { laps_destroy(c); return cuda_fail(e, "laps_create"); }
+    *out = c;
+    return LAPS_OK;
+}
+
+void laps_destroy(laps_ctx* c) {
+    if (!c) return;
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+laps_status laps_set_truth(laps_ctx* c, const double* Ex2, const double* Varx2) {
+    if (!c || !Ex2 || !Varx2) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    std::vector<double> a(c->d_pad, 0.0), b(c->d_pad, 1.0);
+    for (int i = 0; i < c->d; ++i) {
+        if (!(Varx2[i] > 0)) return fail(LAPS_ERR_INVALID_ARG, "Varx2 must be > 0");
+        a[i] = Ex2[i];
+        b[i] = Varx2[i];
+    }
+    CK(cudaMemcpy(c->Ex2, a.data(), c->d_pad * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->Varx2, b.data(), c->d_pad * 8, cudaMemcpyHostToDevice));
+    c->have_truth = true;
+    return LAPS_OK;
+}
+
+laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t seed, void* stream) {
+    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
+    if (x0 && !aligned(x0, 4)) return fail(LAPS_ERR_INVALID_ARG, "x0 must be 4-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->seed = seed;
+    Hyper h;
+    std::memset(&h, 0, sizeof(h));
+    h.phase = 0;
+    h.t = 0;
+    h.t_switch = -1;
+    h.integ = INTEG_LF;
+    h.grads = 1;
+    h.b2_first_t = -1;
+    h.b2_first_grads = -1;
+    h.b2_first_ns = NAN;
+    h.eevpd = h.eevpd_wanted = h.dtilde = h.max_delta = h.acc = NAN;
+    h.b2_max = h.b2_avg = NAN;
+    CK(cudaMemcpyAsync(c->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(c->win, 0, (size_t)c->T * c->d_pad * 8, st));
+    CK(cudaMemsetAsync(c->win_s1, 0, c->d_pad * 8, st));
+    CK(cudaMemsetAsync(c->win_s2, 0, c->d_pad * 8, st));
+    CK(cudaMemsetAsync(c->var_y, 0, c->d_pad * 8, st));
+    fill_kernel<<<grid_for(c->d_pad), 256, 0, st>>>(c->sigma, 1.0f, c->d_pad);
+    CK(cudaGetLastError());
+    // keep the caller's stream synchronous with the host copy of h above
+    CK(cudaStreamSynchronize(st));
+    c->initialized = true;
+    return launch_resident(c, 0, 1, x0, (float)x0_scale, st);
+}
+
+laps_status laps_step(laps_ctx* c, int n_iters, void* stream) {
+    if (!c || n_iters < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (!c->initialized) return fail(LAPS_ERR_INVALID_ARG, "laps_init has not run");
+    if (n_iters == 0) return LAPS_OK;
+    return launch_resident(c, 1, n_iters, nullptr, 0.0f, (cudaStream_t)stream);
+}
+
+laps_status laps_run(laps_ctx* c, void* stream) {
+    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
+    return laps_step(c, c->cfg.n_total_steps + 1, stream);
+}
+
+laps_status laps_adapt_freeze(laps_ctx* c, int frozen) {
+    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
+    CK(cudaStreamSynchronize(c->last_stream));
+    Hyper h;
+    CK(cudaMemcpy(&h, c->hyper, sizeof(h), cudaMemcpyDeviceToHost));
+    h.adapting = frozen ? 0 : 1;
+    CK(cudaMemcpy(c->hyper, &h, sizeof(h), cudaMemcpyHostToDevice));
+    return LAPS_OK;
+}
+
+laps_status laps_sample(const laps_ctx* c, float* x_out, void* stream) {
+    if (!c || !x_out || !aligned(x_out, 4)) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    unpack_rows_kernel<<<grid_for(c->M * c->d), 256, 0, st>>>(c->y, c->sigma, x_out, c->M, c->d,
+                                                             c->d_pad);
+    CK(cudaGetLastError());
+    return LAPS_OK;
+}
+
+laps_status laps_get_state(const laps_ctx* c, float* y, float* u, float* g, double* logp,
+                           float* sigma, void* stream) {
+    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
+    cudaStream_t st = (cudaStream_t)stream;
+    const float* src[3] = {c->y, c->u, c->g};
+    float* dst[3] = {y, u, g};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        if (!aligned(dst[k], 4)) return fail(LAPS_ERR_INVALID_ARG, "misaligned output");
+        unpack_rows_kernel<<<grid_for(c->M * c->d), 256, 0, st>>>(src[k], nullptr, dst[k], c->M,
+                                                                 c->d, c->d_pad);
+        CK(cudaGetLastError());
+    }
+    if (logp) CK(cudaMemcpyAsync(logp, c->logp, c->M * 8, cudaMemcpyDeviceToDevice, st));
+    if (sigma) CK(cudaMemcpyAsync(sigma, c->sigma, c->d * 4, cudaMemcpyDeviceToDevice, st));
+    return LAPS_OK;
+}
+
+static laps_status read_status(laps_ctx* c) {
+    CK(cudaStreamSynchronize(c->last_stream));
+    int s = 0;
+    CK(cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
+    if (s != 0) return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
+    return LAPS_OK;
+}
+
+laps_status laps_get_stats(laps_ctx* c, laps_stats* o) {
+    if (!c || !o) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    laps_status st = read_status(c);
+    Hyper h;
+    CK(cudaMemcpy(&h, c->hyper, sizeof(h), cudaMemcpyDeviceToHost));
+    std::memset(o, 0, sizeof(*o));
+    o->phase = h.phase;
+    o->t = h.t;
+    o->t_switch = h.t_switch;
+    o->integrator = h.integ;
+    o->adapting = h.adapting;
+    o->done = h.done;
+    o->iterations = h.iters;
+    o->nonfinite_total = h.nonfinite_total;
+    o->grads = h.grads;
+    o->eps = h.eps;
+    o->L = h.L;
+    o->eevpd = h.eevpd;
+    o->eevpd_wanted = h.eevpd_wanted;
+    o->dtilde = h.dtilde;
+    o->max_delta = h.max_delta;
+    o->acc = h.acc;
+    o->b2_max = h.b2_max;
+    o->b2_avg = h.b2_avg;
+    o->sum_var = h.sum_var;
+    o->b2_first_t = h.b2_first_t;
+    o->b2_first_grads = h.b2_first_grads;
+    o->b2_first_ns = h.b2_first_ns;
+    return st;
+}
+
+laps_status laps_get_trace(laps_ctx* c, laps_trace_row* rows, int cap, int* n) {
+    if (!c || !n) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    CK(cudaStreamSynchronize(c->last_stream));
+    Hyper h;
+    CK(cudaMemcpy(&h, c->hyper, sizeof(h), cudaMemcpyDeviceToHost));
+    const int avail = std::min(h.iters + 1, c->trace_cap);
+    *n = avail;
+    if (rows && cap > 0)
+        CK(cudaMemcpy(rows, c->trace, (size_t)std::min(cap, avail) * sizeof(laps_trace_row),
+                      cudaMemcpyDeviceToHost));
+    return LAPS_OK;
+}
+
+// checkpoint layout: header, then every device buffer the run depends on
+struct CkptHeader {
+    char magic[8];
+    int64_t M;
+    int d, d_pad, T, trace_cap;
+    uint64_t seed;
+    int have_truth, pad_;
+};
+
+static std::vector<std::pair<void*, size_t>> ckpt_buffers(laps_ctx* c) {
+    const size_t Md = (size_t)c->M * c->d_pad;
+    return {{c->y, Md * 4},           {c->u, Md * 4},          {c->g, Md * 4},
+            {c->logp, (size_t)c->M * 8}, {c->sigma, (size_t)c->d_pad * 4},
+            {c->var_y, (size_t)c->d_pad * 8},
+            {c->win, (size_t)c->T * c->d_pad * 8}, {c->win_s1, (size_t)c->d_pad * 8},
+            {c->win_s2, (size_t)c->d_pad * 8},   {c->Ex2, (size_t)c->d_pad * 8},
+            {c->Varx2, (size_t)c->d_pad * 8},    {c->hyper, sizeof(Hyper)},
+            {c->trace, (size_t)c->trace_cap * sizeof(laps_trace_row)}};
+}
+
+laps_status laps_checkpoint(laps_ctx* c, void* blob, size_t* size) {
+    if (!c || !size) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    auto bufs = ckpt_buffers(c);
+    size_t need = sizeof(CkptHeader);
+    for (auto& b : bufs) need += b.second;
+    if (!blob) { *size = need; return LAPS_OK; }
+    if (*size < need) return fail(LAPS_ERR_INVALID_ARG, "checkpoint buffer too small");
+    CK(cudaStreamSynchronize(c->last_stream));
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LAPSCK1", 8);
+    h.M = c->M; h.d = c->d; h.d_pad = c->d_pad; h.T = c->T; h.trace_cap = c->trace_cap;
+    h.seed = c->seed; h.have_truth = c->have_truth;
+    char* p = static_cast<char*>(blob);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    for (auto& b : bufs) {
+        CK(cudaMemcpy(p, b.first, b.second, cudaMemcpyDeviceToHost));
+        p += b.second;
+    }
+    *size = need;
+    return LAPS_OK;
+}
+
+laps_status laps_restore(laps_ctx* c, const void* blob, size_t size) {
+    if (!c || !blob) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    CkptHeader h;
+    if (size < sizeof(h)) return fail(LAPS_ERR_INVALID_ARG, "checkpoint too small");
+    std::memcpy(&h, blob, sizeof(h));
+    if (std::memcmp(h.magic, "LAPSCK1", 8) != 0 || h.M != c->M || h.d != c->d ||
+        h.d_pad != c->d_pad || h.T != c->T || h.trace_cap != c->trace_cap)
+        return fail(LAPS_ERR_INVALID_ARG, "checkpoint does not match this context");
+    auto bufs = ckpt_buffers(c);
+    size_t need = sizeof(h);
+    for (auto& b : bufs) need += b.second;
+    if (size < need) return fail(LAPS_ERR_INVALID_ARG, "checkpoint truncated");
+    CK(cudaStreamSynchronize(c->last_stream));
+    const char* p = static_cast<const char*>(blob) + sizeof(h);
+    for (auto& b : bufs) {
+        CK(cudaMemcpy(b.first, p, b.second, cudaMemcpyHostToDevice));
+        p += b.second;
+    }
+    c->seed = h.seed;
+    c->have_truth = h.have_truth != 0;
+    c->initialized = true;
+    CK(cudaMemset(c->status, 0, sizeof(int)));
+    return LAPS_OK;
+}
+
+laps_status laps_get_launch_info(const laps_ctx* c, laps_launch_info* o) {
+    if (!c || !o) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    o->chains_per_block = c->threads / c->lpc;
+    o->lanes_per_chain = c->lpc;
+    o->coords_per_lane = c->cpl;
+    o->threads = c->threads;
+    o->blocks = c->G;
+    o->resident = 1;
+    return LAPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// laps_internal.h -- opaque handle layouts and host helpers of liblaps.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "laps_params.h"
+#include "laps_resident.cuh"
+
+struct laps_target {
+    laps_target_desc desc;
+    int kind = 0, d = 0, d_pad = 0;
+    float* prec_pad = nullptr;  // GAUSS_DIAG precisions, zero padded to d_pad (owned)
+};
+
+struct laps_ctx {
+    const laps_target* tg = nullptr;
+    int64_t M = 0;
+    laps_config cfg{};
+    int d = 0, d_pad = 0, T = 0, trace_cap = 0;
+    // ensemble state (sampler coordinates, [M][d_pad]) and phase machine
+    float *y = nullptr, *u = nullptr, *g = nullptr, *sigma = nullptr;
+    double* logp = nullptr;
+    double *part_coord = nullptr, *part_chain = nullptr, *part_slice = nullptr;
+    double *var_y = nullptr, *win = nullptr, *win_s1 = nullptr, *win_s2 = nullptr;
+    double *Ex2 = nullptr, *Varx2 = nullptr;
+    laps::Hyper* hyper = nullptr;
+    laps_trace_row* trace = nullptr;
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    laps::Coefs* coefs = nullptr;
+    std::vector<void*> allocs;
+    // launch shape
+    int lpc = 0, cpl = 0, threads = 0, G = 0;
+    size_t smem = 0;
+    const void* fn = nullptr;
+    cudaStream_t last_stream = nullptr;
+    uint64_t seed = 0;
+    bool initialized = false, have_truth = false;
+};
+
+namespace laps {
+laps_status fail(laps_status st, const std::string& msg);
+laps_status cuda_fail(cudaError_t e, const char* what);
+}  // namespace laps

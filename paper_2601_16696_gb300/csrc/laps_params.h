@@ -1,0 +1,73 @@
+// laps_params.h -- parameter and state blocks shared by the host API and the
+// kernels (plain structs, no CUDA types, included by .cu and .cpp files).
+#pragma once
+#include <cstdint>
+
+#include "../../include/laps.h"
+
+namespace laps {
+
+// Hyperparameters and phase machine of Alg. 1 (identical in every block).
+struct Hyper {
+    double eps, L, lo, hi, a_target;
+    double eps_used;
+    double eevpd, eevpd_wanted, dtilde, max_delta, acc, b2_max, b2_avg, sum_var;
+    double b2_first_ns;
+    long long grads, b2_first_grads;
+    unsigned long long t0_ns;
+    int phase, t, t_switch, integ, adapting, p, done, iters, win_n, nonfinite_total;
+    int nonfinite_last, b2_first_t, pad_[2];
+};
+
+enum : int { TGT_GAUSS = 0, TGT_BANANA = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3 };
+enum : int { INTEG_LF = 0, INTEG_MN2 = 1, INTEG_MN4 = 2 };
+enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4 };
+
+// per-coordinate sums kept per block, and per-chain / per-slice scalars
+enum : int { NQ = 4 };                                   // sum y, y^2, g, y g
+enum : int { CS_DSUM = 0, CS_DSQ, CS_NFIN, CS_NBAD, CS_ASUM, NCS };
+enum : int { SL_VAR = 0, SL_DV, SL_MAXDEL, SL_B2SUM, SL_B2MAX, NSL };
+
+struct KParams {
+    // problem
+    int M, d, d_pad, nblk;
+    int kind;
+    float inv_s2;       // banana: 1 / sb^2
+    float inv_sv2;      // funnel: 1 / sv^2
+    const float* prec;  // gauss: [d_pad], zero padded
+    // ensemble state, sampler coordinates, [M][d_pad]
+    float *y, *u, *g;
+    double* logp;       // [M]
+    float* sigma;       // [d_pad] preconditioner (1 before the switch)
+    const float* x0;    // init: [M][d] caller layout, or nullptr for Philox
+    float x0_scale;
+    // scratch (global)
+    double* part_coord;  // [NQ][d_pad][G]
+    double* part_chain;  // [NCS][G]
+    double* part_slice;  // [NSL][G]
+    double* var_y;       // [d_pad] ensemble variance of the last iteration
+    double* win;         // [T][d_pad] E[x_i^2] ring
+    double* win_s1;      // [d_pad] running window sum
+    double* win_s2;      // [d_pad] running window sum of squares
+    const double* Ex2;   // [d_pad] truth or nullptr
+    const double* Varx2;
+    Hyper* hyper;
+    laps_trace_row* trace;
+    int trace_cap;
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* status;
+    // configuration
+    double C, alpha, switch_tol, acc_tol, adj_L_factor, eps0, a_target_mn2, a_target_mn4;
+    double stop_b2;
+    int stop_b2_max;
+    int T, n_total, N, mn4_min_dim, eevpd_centered, adjusted, force_switch_at;
+    long long timeout_ns;
+    uint32_t seed_lo, seed_hi, pid;
+    int mode;     // 0: initialise, 1: iterate
+    int n_iters;  // iterations of this launch
+    int G;        // blocks in the grid
+    int bar_extra;  // extra arrivals every barrier waits for (test hook; 0 normally)
+};
+
+}  // namespace laps

@@ -1,0 +1,137 @@
+// laps_target.cu -- stand-alone log-density + gradient of the built-in targets
+// (the forward and hand-written backward used by the sampler), for M points in
+// the caller's [M][d] layout.  One warp per point; log p is summed with
+// compensated float-float arithmetic and rounded to FP32 at the end.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "laps_internal.h"
+
+namespace laps {
+
+__device__ __forceinline__ ff warp_sum_ff(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    return v;
+}
+
+__global__ void target_logp_grad_kernel(int kind, const float* __restrict__ x, int64_t M, int d,
+                                        const float* __restrict__ prec, float inv_s2, float inv_sv2,
+                                        float* __restrict__ logp, float* __restrict__ grad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (m >= M) return;  // whole warps exit together
+    const float* xm = x + m * d;
+    float* gm = grad + m * d;
+    ff part = ff_make(0.0f);
+    if (kind == TGT_GAUSS) {
+        for (int i = lane; i < d; i += 32) {
+            const float gx = -prec[i] * xm[i];
+            gm[i] = gx;
+            part = ff_add(part, 0.5f * gx * xm[i]);
+        }
+        part = warp_sum_ff(part);
+    } else if (kind == TGT_BANANA) {
+        for (int k = lane; 2 * k + 1 < d; k += 32) {
+            const float a = xm[2 * k], b = xm[2 * k + 1];
+            const float r = fmaf(-a, a, b);
+            const float ris = r * inv_s2;
+            part = ff_add(part, fmaf(-0.5f * a, a, -0.5f * r * ris));
+            gm[2 * k] = fmaf(2.0f * a, ris, -a);
+            gm[2 * k + 1] = -ris;
+        }
+        part = warp_sum_ff(part);
+    } else {  // funnel
+        float ss = 0.0f;
+        for (int i = 1 + lane; i < d; i += 32) ss = fmaf(xm[i], xm[i], ss);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float v = xm[0];
+        const float ev = expf(-v);
+        const float n = (float)(d - 1);
+        part = ff_make(-0.5f * v * v * inv_sv2);
+        part = ff_add(part, -0.5f * n * v);
+        part = ff_add(part, -0.5f * ev * ss);
+        for (int i = 1 + lane; i < d; i += 32) gm[i] = -xm[i] * ev;
+        if (lane == 0) gm[0] = fmaf(-v, inv_sv2, -0.5f * n) + 0.5f * ev * ss;
+    }
+    if (lane == 0) logp[m] = part.hi + part.lo;
+}
+
+}  // namespace laps
+
+using namespace laps;
+
+extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
+                                             float* logp, float* grad, void* stream) {
+    if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (tg->kind == TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "use the logreg entry points");
+    if (M == 0) return LAPS_OK;
+    const int threads = 256;
+    const int64_t blocks = (M * 32 + threads - 1) / threads;
+    if (blocks > 0x7fffffff) return fail(LAPS_ERR_INVALID_ARG, "M too large");
+    const laps_target_desc& dsc = tg->desc;
+    target_logp_grad_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(
+        tg->kind, x, M, tg->d, tg->prec_pad, (float)(1.0 / (dsc.banana_sb * dsc.banana_sb)),
+        (float)(1.0 / (dsc.funnel_sv * dsc.funnel_sv)), logp, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "target_logp_grad_kernel");
+    return LAPS_OK;
+}
+
+// ---------------------------------------------------------------- random stream
+namespace laps {
+__global__ void philox_kernel(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                              uint4* __restrict__ out, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = philox4x32_10(ctr[k], k0, k1);
+}
+__global__ void normals_kernel(uint32_t k0, uint32_t k1, uint32_t m0, int64_t nm, uint32_t t,
+                               uint32_t tagpid, int64_t d, float* __restrict__ out) {
+    const int64_t nblk = (d + 3) / 4;
+    const int64_t n = nm * nblk;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mm = k / nblk, j = k - mm * nblk;
+        float z[4];
+        normals4((uint32_t)j, m0 + (uint32_t)mm, t, tagpid, k0, k1, z);
+        for (int c = 0; c < 4; ++c)
+            if (4 * j + c < d) out[mm * d + 4 * j + c] = z[c];
+    }
+}
+}  // namespace laps
+
+extern "C" laps_status laps_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
+                                   void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) % 16)
+        return fail(LAPS_ERR_INVALID_ARG, "ctr and out must be 16-byte aligned");
+    if (n == 0) return LAPS_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    philox_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const uint4*>(ctr), (uint32_t)seed, (uint32_t)(seed >> 32),
+        reinterpret_cast<uint4*>(out), n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "philox_kernel");
+}
+
+extern "C" laps_status laps_normals(uint64_t seed, uint32_t m0, int64_t nm, uint32_t t,
+                                    uint32_t tag, uint32_t pid, int64_t d, float* out,
+                                    void* stream) {
+    if (nm < 0 || d < 1 || (nm > 0 && !out) || tag > 255 || pid >= (1u << 24))
+        return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (nm == 0) return LAPS_OK;
+    const int64_t n = nm * ((d + 3) / 4);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    normals_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        (uint32_t)seed, (uint32_t)(seed >> 32), m0, nm, t, tag | (pid << 8), d, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "normals_kernel");
+}

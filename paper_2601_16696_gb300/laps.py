@@ -1,0 +1,309 @@
+"""ctypes binding of liblaps.so (include/laps.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and streams, and raises on any non-OK status.
+There is no fallback: without the built library (``build.py``) every call
+raises ``LapsError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblaps.so")
+
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG = 0, 1, 2, 3
+FP32, MIXED = 0, 1
+LF, MN2, MN4 = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NONFINITE",
+          6: "UNSUPPORTED"}
+
+
+class LapsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("LAPS_ERR_%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class TargetDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("d", C.c_int64), ("prec", C.c_void_p),
+                ("banana_sb", C.c_double), ("funnel_sv", C.c_double), ("n_data", C.c_int64),
+                ("X", C.c_void_p), ("y", C.c_void_p), ("prior_var", C.c_double)]
+
+
+class Config(C.Structure):
+    _fields_ = [("C", C.c_double), ("alpha", C.c_double), ("switch_tol", C.c_double),
+                ("window_frac", C.c_double), ("acc_tol", C.c_double),
+                ("adj_L_factor", C.c_double), ("eps0_coef", C.c_double),
+                ("a_target_mn2", C.c_double), ("a_target_mn4", C.c_double),
+                ("n_total_steps", C.c_int), ("steps_per_proposal", C.c_int),
+                ("mn4_min_dim", C.c_int), ("eevpd_centered", C.c_int), ("adjusted", C.c_int),
+                ("force_switch_at", C.c_int), ("stop_b2", C.c_double), ("stop_b2_max", C.c_int),
+                ("precision", C.c_int), ("barrier_timeout_ns", C.c_int64),
+                ("chains_per_block", C.c_int), ("lanes_per_chain", C.c_int),
+                ("coords_per_lane", C.c_int), ("barrier_extra_arrivals", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("phase", C.c_int), ("t", C.c_int), ("t_switch", C.c_int),
+                ("integrator", C.c_int), ("adapting", C.c_int), ("done", C.c_int),
+                ("iterations", C.c_int), ("nonfinite_total", C.c_int), ("grads", C.c_longlong),
+                ("eps", C.c_double), ("L", C.c_double), ("eevpd", C.c_double),
+                ("eevpd_wanted", C.c_double), ("dtilde", C.c_double), ("max_delta", C.c_double),
+                ("acc", C.c_double), ("b2_max", C.c_double), ("b2_avg", C.c_double),
+                ("sum_var", C.c_double), ("b2_first_t", C.c_int),
+                ("b2_first_grads", C.c_longlong), ("b2_first_ns", C.c_double)]
+
+
+class TraceRow(C.Structure):
+    _fields_ = [("phase", C.c_int), ("t", C.c_int), ("eps", C.c_double), ("L", C.c_double),
+                ("eps_used", C.c_double), ("eevpd", C.c_double), ("eevpd_wanted", C.c_double),
+                ("dtilde", C.c_double), ("max_delta", C.c_double), ("acc", C.c_double),
+                ("b2_max", C.c_double), ("b2_avg", C.c_double), ("sum_var", C.c_double),
+                ("nonfinite", C.c_int), ("adapting", C.c_int), ("grads", C.c_longlong),
+                ("time_ns", C.c_double)]
+
+
+class LaunchInfo(C.Structure):
+    _fields_ = [("chains_per_block", C.c_int), ("lanes_per_chain", C.c_int),
+                ("coords_per_lane", C.c_int), ("threads", C.c_int), ("blocks", C.c_int),
+                ("resident", C.c_int)]
+
+
+def _as_dict(s):
+    return {n: getattr(s, n) for n, _ in s._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = C.c_void_p
+
+# name -> (restype, argtypes); the list is also the ABI the tests check
+SIGNATURES = {
+    "laps_config_default": (None, [C.POINTER(Config)]),
+    "laps_last_error": (C.c_char_p, []),
+    "laps_version": (C.c_char_p, []),
+    "laps_target_create": (C.c_int, [C.POINTER(TargetDesc), C.POINTER(_vp)]),
+    "laps_target_destroy": (None, [_vp]),
+    "laps_target_logp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "laps_create": (C.c_int, [_vp, C.c_int64, C.POINTER(Config), C.POINTER(_vp)]),
+    "laps_destroy": (None, [_vp]),
+    "laps_init": (C.c_int, [_vp, _vp, C.c_double, C.c_uint64, _vp]),
+    "laps_step": (C.c_int, [_vp, C.c_int, _vp]),
+    "laps_run": (C.c_int, [_vp, _vp]),
+    "laps_adapt_freeze": (C.c_int, [_vp, C.c_int]),
+    "laps_sample": (C.c_int, [_vp, _vp, _vp]),
+    "laps_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "laps_set_truth": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "laps_get_stats": (C.c_int, [_vp, C.POINTER(Stats)]),
+    "laps_get_trace": (C.c_int, [_vp, C.POINTER(TraceRow), C.c_int, C.POINTER(C.c_int)]),
+    "laps_checkpoint": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t)]),
+    "laps_restore": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "laps_philox": (C.c_int, [_vp, C.c_uint64, _vp, C.c_int64, _vp]),
+    "laps_normals": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_uint32, C.c_uint32,
+                               C.c_uint32, C.c_int64, _vp, _vp]),
+    "laps_get_launch_info": (C.c_int, [_vp, C.POINTER(LaunchInfo)]),
+}
+
+
+def lib(path: str | None = None):
+    """Load liblaps.so (raises LapsError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise LapsError(2, "liblaps.so not built (%s); run paper_2601_16696_gb300/build.py"
+                                % p)
+            L = C.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise LapsError(st, lib().laps_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float32):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor of %s" % dtype)
+    return C.c_void_p(t.data_ptr())
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    lib().laps_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Target:
+    """A built-in target (device copies of its parameters are kept alive here)."""
+
+    def __init__(self, kind: int, d: int, prec=None, banana_sb: float = 0.1,
+                 funnel_sv: float = 3.0, X=None, y=None, prior_var: float = 1.0,
+                 device="cuda"):
+        self.kind, self.d = kind, d
+        self._keep = []
+        desc = TargetDesc(kind, d, None, banana_sb, funnel_sv, 0, None, None, prior_var)
+        if prec is not None:
+            p = torch.as_tensor(prec, dtype=torch.float32, device=device).contiguous()
+            self._keep.append(p)
+            desc.prec = p.data_ptr()
+        if X is not None:
+            Xt = torch.as_tensor(X, dtype=torch.float32, device=device).contiguous()
+            yt = torch.as_tensor(y, dtype=torch.float32, device=device).contiguous()
+            self._keep += [Xt, yt]
+            desc.X, desc.y, desc.n_data = Xt.data_ptr(), yt.data_ptr(), Xt.shape[0]
+        h = C.c_void_p()
+        _check(lib().laps_target_create(C.byref(desc), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, pr, device="cuda"):
+        return cls(pr.kind, pr.d, prec=pr.prec, banana_sb=pr.banana_sb, funnel_sv=pr.funnel_sv,
+                   X=pr.X, y=pr.y, prior_var=pr.prior_var, device=device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def logp_grad(self, x: torch.Tensor, stream=None):
+        """log p [M] and grad log p [M, d] of the rows of x (FP32, CUDA)."""
+        x = x.contiguous()
+        M = x.shape[0]
+        logp = torch.empty(M, dtype=torch.float32, device=x.device)
+        grad = torch.empty_like(x)
+        _check(lib().laps_target_logp_grad(self._h, _ptr(x), M, _ptr(logp), _ptr(grad),
+                                           _stream(stream)))
+        return logp, grad
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.laps_target_destroy(h)
+            self._h = None
+
+
+class Sampler:
+    """One LAPS run of M chains on a Target (Algorithm 1 on the GPU)."""
+
+    def __init__(self, target: Target, M: int, config: Config | None = None, **cfg_kw):
+        self.target, self.M, self.d = target, M, target.d
+        self.config = config if config is not None else default_config(**cfg_kw)
+        h = C.c_void_p()
+        _check(lib().laps_create(target.handle, M, C.byref(self.config), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.laps_destroy(h)
+            self._h = None
+
+    def set_truth(self, Ex2, Varx2):
+        a = (C.c_double * self.d)(*[float(v) for v in Ex2])
+        b = (C.c_double * self.d)(*[float(v) for v in Varx2])
+        _check(lib().laps_set_truth(self._h, a, b))
+
+    def init(self, x0: torch.Tensor | None = None, x0_scale: float = 1.0, seed: int = 0,
+             stream=None):
+        self._x0 = x0.contiguous() if x0 is not None else None
+        _check(lib().laps_init(self._h, _ptr(self._x0), x0_scale, seed, _stream(stream)))
+
+    def step(self, n: int = 1, stream=None):
+        _check(lib().laps_step(self._h, n, _stream(stream)))
+
+    def run(self, stream=None):
+        _check(lib().laps_run(self._h, _stream(stream)))
+
+    def freeze(self, frozen: bool = True):
+        _check(lib().laps_adapt_freeze(self._h, int(frozen)))
+
+    def sample(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.M, self.d, dtype=torch.float32, device="cuda")
+        _check(lib().laps_sample(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def state(self, stream=None):
+        y, u, g = (torch.empty(self.M, self.d, dtype=torch.float32, device="cuda")
+                   for _ in range(3))
+        lp = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        sg = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        _check(lib().laps_get_state(self._h, _ptr(y), _ptr(u), _ptr(g),
+                                    _ptr(lp, torch.float64), _ptr(sg), _stream(stream)))
+        return y, u, g, lp, sg
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().laps_get_stats(self._h, C.byref(s)))
+        return _as_dict(s)
+
+    def stats_status(self):
+        """(status code, stats dict) without raising."""
+        s = Stats()
+        st = lib().laps_get_stats(self._h, C.byref(s))
+        return st, _as_dict(s)
+
+    def trace(self) -> list:
+        n = C.c_int(0)
+        _check(lib().laps_get_trace(self._h, None, 0, C.byref(n)))
+        rows = (TraceRow * max(1, n.value))()
+        _check(lib().laps_get_trace(self._h, rows, n.value, C.byref(n)))
+        return [_as_dict(rows[i]) for i in range(n.value)]
+
+    def checkpoint(self) -> bytes:
+        sz = C.c_size_t(0)
+        _check(lib().laps_checkpoint(self._h, None, C.byref(sz)))
+        buf = C.create_string_buffer(sz.value)
+        _check(lib().laps_checkpoint(self._h, buf, C.byref(sz)))
+        return buf.raw[:sz.value]
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().laps_restore(self._h, buf, len(blob)))
+
+    def launch_info(self) -> dict:
+        li = LaunchInfo()
+        _check(lib().laps_get_launch_info(self._h, C.byref(li)))
+        return _as_dict(li)
+
+
+def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Philox4x32-10 of int32 counters ctr [n, 4] (CUDA), as the sampler draws it."""
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib().laps_philox(_ptr(ctr, torch.int32), seed, _ptr(out, torch.int32), ctr.shape[0],
+                             _stream(stream)))
+    return out
+
+
+def normals(seed: int, m0: int, nm: int, t: int, tag: int, pid: int, d: int,
+            stream=None) -> torch.Tensor:
+    out = torch.empty(nm, d, dtype=torch.float32, device="cuda")
+    _check(lib().laps_normals(seed, m0, nm, t & 0xFFFFFFFF, tag, pid, d, _ptr(out),
+                              _stream(stream)))
+    return out
