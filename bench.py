@@ -1,0 +1,303 @@
+"""Benchmark of the LAPS hot path on GB300: one JSON line on stdout.
+
+A step is one complete LAPS run (Algorithm 1: initialisation, the unadjusted
+phase, the switch, the adjusted phase, the samples) of the workload: the
+banana target, d = 100, M = 4096 chains, 5000 integrator steps.  The paper's
+default switch rule would keep this ensemble unadjusted (its window statistic
+stays above 0.01 at M = 4096), so the timed runs switch after the first window
+(1000 steps, the paper's "number of unadjusted steps" ablation knob) and run
+MAMS proposals for the remaining 4000 steps.
+
+value      chain-gradient-evals/s = M x gradient evaluations per chain / time,
+           inputs resident on the device, CUDA events on the launching stream.
+e2e        the same metric through the public API with host buffers: x0 copied
+           from pinned host memory and the samples copied back in the timed
+           region.
+time_to_b2 wall time (CUDA events) of runs that stop at b^2_max < 0.01.
+roofline   the persistent kernel against the FP32 ALU issue rate.
+cpu_baseline  the FP64 oracle on the host cores on a bounded sample.
+
+--impl reference runs the oracle (the only reference this path has) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chain-gradient-evals/sec and wall time to second-moment bias^2<0.01, 1 GB300"
+UNIT = "chain-grad-evals/s"
+WORKLOAD = dict(name="banana_d100", d=100, M=4096, n_steps=5000, switch_at=1000)
+# algorithmic ALU operations per coordinate and gradient evaluation (the design doc
+# "Roofline of the resident kernel"): LF unadjusted step and MN2 adjusted step
+ALU_OPS_LF = 96.0
+ALU_OPS_MN2_PER_GRAD = 70.0
+
+
+def _rank_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 8
+                          for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _cpu_baseline(pr, seconds_hint=True):
+    """The oracle, as it stands, on the host cores: the first 500 unadjusted
+    iterations of the same ensemble (all M chains)."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    tg = oracle.OracleTarget(pr.kind, pr.d, prec=pr.prec, banana_sb=pr.banana_sb,
+                             funnel_sv=pr.funnel_sv)
+    run = oracle.OracleLAPS(tg, pr.x0, seed=0, n_total_steps=pr.n_steps)
+    n_it = 500
+    t0 = time.perf_counter()
+    run.iterate(n_it)
+    dt = time.perf_counter() - t0
+    grads = run.trace[-1]["grads"] - 1
+    return {"value": pr.M * grads / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle, %d chains x first %d unadjusted iterations of %s (%.1f s)"
+                      % (pr.M, n_it, pr.name, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return 0
+    from paper_2601_16696_gb300 import workloads
+    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(_cpu_baseline(pr))
+    timed = vals[args.warmup:]
+    v = statistics.mean(r["value"] for r in timed)
+    ms = statistics.mean(1e3 * pr.M * 500 / r["value"] for r in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s_M%d (oracle sample: first 500 unadjusted iterations)"
+                       % (pr.name, pr.M)},
+            "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v,
+                                                                                    "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="laps", choices=["laps", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2601_16696_gb300 import build, laps, workloads
+    build.build()
+
+    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
+    tg = laps.Target.from_problem(pr)
+    cfg = dict(n_total_steps=pr.n_steps, force_switch_at=WORKLOAD["switch_at"])
+    sampler = laps.Sampler(tg, pr.M, **cfg)
+    sampler.set_truth(pr.Ex2, pr.Varx2)
+    stopper = laps.Sampler(tg, pr.M, stop_b2=0.01, stop_b2_max=1, **cfg)
+    stopper.set_truth(pr.Ex2, pr.Varx2)
+    x0_dev = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
+    x0_host = torch.tensor(pr.x0, dtype=torch.float32).pin_memory()
+    out_host = torch.empty(pr.M, pr.d, dtype=torch.float32).pin_memory()
+    x0_e2e = torch.empty_like(x0_dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    seed_base = 1000 * rank
+
+    def one_run(s, seed):
+        s.init(x0_dev, seed=seed)
+        s.run()
+
+    def timed(fn, n, seed0):
+        ts = []
+        for k in range(n):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(seed0 + k)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    # ---- warm-up
+    for k in range(args.warmup):
+        one_run(sampler, seed_base + k)
+        one_run(stopper, seed_base + k)
+    torch.cuda.synchronize()
+    st = sampler.stats()
+    grads = st["grads"]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing (the headline value)
+    barrier()
+    with Clocks(local) as clk:
+        ts = timed(lambda sd: one_run(sampler, sd), args.steps, seed_base + 100)
+    barrier()
+    st = sampler.stats()
+    assert st["done"] and st["grads"] == grads, st
+    ms = statistics.mean(ts)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * pr.M * grads / (ms * 1e-3)
+
+    # ---- the kernel's own duration and its ALU roofline
+    info = sampler.launch_info()
+    tr = sampler.trace()
+    n_unadj = sum(1 for r in tr[1:] if r["phase"] == 0)
+    n_adj_grads = grads - 1 - n_unadj
+    k_ms = []
+    for k in range(args.steps):
+        sampler.init(x0_dev, seed=seed_base + 200 + k)
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sampler.run()
+        b.record(stream)
+        b.synchronize()
+        k_ms.append(a.elapsed_time(b))
+    kms = statistics.mean(k_ms)
+    coord = pr.M * pr.d
+    ops = coord * (n_unadj * ALU_OPS_LF + n_adj_grads * ALU_OPS_MN2_PER_GRAD)
+    clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or 1455.0
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = nsm * 128 * mhz * 1e6 / 1e9  # FP32-pipe lane issue rate, Gop/s
+    achieved = ops / (kms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "resident_banana_d100_traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get("bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "laps_resident_kernel<banana,%d,%d>" % (info["lanes_per_chain"],
+                                                                   info["coords_per_lane"]),
+                "kernel_ms": kms,
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (measured median)" % (nsm, mhz)}
+
+    # ---- wall time to b^2_max < 0.01
+    t2 = timed(lambda sd: one_run(stopper, sd), args.steps, seed_base + 300)
+    s2 = stopper.stats()
+    time_to_b2 = {"ms": statistics.mean(t2), "b2": "b2_max", "threshold": 0.01,
+                  "reached": s2["b2_max"] < 0.01, "t": s2["t"], "grads_per_chain": s2["grads"],
+                  "phase_at_stop": s2["phase"]}
+
+    # ---- end to end through the public API with host buffers
+    def e2e_run(seed):
+        x0_e2e.copy_(x0_host, non_blocking=True)
+        sampler.init(x0_e2e, seed=seed)
+        sampler.run()
+        sampler.sample(out=x0_e2e)
+        out_host.copy_(x0_e2e, non_blocking=True)
+
+    te = timed(e2e_run, args.steps, seed_base + 400)
+    e2e_ms = statistics.mean(te)
+    e2e = {"value": world * pr.M * grads / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4,
+           "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
+                       "switch": "after %d unadjusted steps (first full window)"
+                                 % WORKLOAD["switch_at"],
+                       "grads_per_chain": grads, "l2": "flushed (256 MB write) between runs",
+                       "launch": info, "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "time_to_b2": time_to_b2, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline(pr)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -94,6 +94,8 @@ typedef struct {
     int eevpd_centered;      /* 1: EEVPD = Var[Delta]/d (Eq. EEVPD); 0: mean Delta^2/d (Alg. 1) */
     int adjusted;            /* 0: never switch (unadjusted only) */
     int force_switch_at;     /* > 0: switch after exactly this many unadjusted steps */
+    double fixed_eps;        /* > 0: unadjusted step size held at this value (the fixed-step
+                                comparison of App. A, Fig. "stepsize"); 0: Sec. 3.1 controller */
     double stop_b2;          /* > 0 (needs laps_set_truth): finish once b^2 < stop_b2 */
     int stop_b2_max;         /* 0: use b^2_avg for stop_b2; 1: use b^2_max */
     laps_precision precision;

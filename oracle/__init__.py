@@ -53,7 +53,8 @@ class Config(C.Structure):
                 ("a_target_mn2", C.c_double), ("a_target_mn4", C.c_double),
                 ("n_total_steps", C.c_int), ("steps_per_proposal", C.c_int),
                 ("mn4_min_dim", C.c_int), ("eevpd_centered", C.c_int), ("adjusted", C.c_int),
-                ("force_switch_at", C.c_int)]
+                ("force_switch_at", C.c_int), ("fixed_eps", C.c_double),
+                ("round_state_f32", C.c_int)]
 
 
 class TraceRow(C.Structure):

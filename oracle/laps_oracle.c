@@ -222,6 +222,15 @@ int ora_integrator_coefs(int integ, double* b, double* a) {
     return 0;
 }
 
+/* Diagnostic only (round_state_f32): round a vector to binary32 after a map,
+ * to measure how much a binary32 chain state perturbs the run.  Set per
+ * iteration from the state's config, before the chain loop. */
+static int g_round_f32 = 0;
+static void round_f32(int64_t d, double* v) {
+    if (!g_round_f32) return;
+    for (int64_t i = 0; i < d; ++i) v[i] = (double)(float)v[i];
+}
+
 /* Eq. "integrator": Phi = B_{b1 eps} A_{a1 eps} B_{b2 eps} ... B_{bK eps}.
  * Energy error: each A adds -log p(x') + log p(x), each B its kinetic term. */
 static double phi_y(const ora_target* tg, const double* sigma, int integ, double eps,
@@ -232,9 +241,12 @@ static double phi_y(const ora_target* tg, const double* sigma, int integ, double
     double delta = 0.0;
     for (int k = 0; k < K; ++k) {
         delta += ora_B(d, b[k] * eps, g, u);
+        round_f32(d, u);
         if (k < K - 1) {
             ora_A(d, a[k] * eps, u, y);
+            round_f32(d, y);
             double lp_new = eval_y(tg, sigma, y, g, xbuf);
+            round_f32(d, g);
             delta += -lp_new + *logp;
             *logp = lp_new;
         }
@@ -328,6 +340,8 @@ void ora_config_default(ora_config* c) {
     c->eevpd_centered = 1;
     c->adjusted = 1;
     c->force_switch_at = 0;
+    c->fixed_eps = 0.0;
+    c->round_state_f32 = 0;
 }
 
 struct ora_state {
@@ -403,7 +417,7 @@ ora_state* ora_create(const ora_target* tg, const ora_config* cfg, int64_t M, co
             for (int64_t i = 0; i < d; ++i) um[i] /= n2;
         }
     }
-    s->eps = cfg->eps0_coef * sqrt((double)d);
+    s->eps = cfg->fixed_eps > 0 ? cfg->fixed_eps : cfg->eps0_coef * sqrt((double)d);
     s->L = ora_L_of(M, d, s->y, cfg->alpha);
     s->phase = 0;
     s->t = 0;
@@ -525,10 +539,12 @@ static void unadjusted_chain(ora_state* s, int64_t m, double* z) {
     ora_normals(s->seed, (uint32_t)m, (uint32_t)s->t, ORA_TAG_O1, s->pid, d, z);
     for (int64_t i = 0; i < d; ++i) z[i] *= inv_sqrt_d;
     ora_O(d, 0.5 * s->eps, s->L, z, u);
+    round_f32(d, u);
     s->delta[m] = phi_y(&s->tg, NULL, ORA_LF, s->eps, y, u, g, &s->logp[m], s->xbuf + m * d);
     ora_normals(s->seed, (uint32_t)m, (uint32_t)s->t, ORA_TAG_O2, s->pid, d, z);
     for (int64_t i = 0; i < d; ++i) z[i] *= inv_sqrt_d;
     ora_O(d, 0.5 * s->eps, s->L, z, u);
+    round_f32(d, u);
 
     s->bad[m] = !finite_chain(s, m);
     if (s->bad[m]) { /* revert the chain to its state before the step */
@@ -564,10 +580,12 @@ static double mams_core(const ora_target* tg, const double* sigma, int integ, do
         ora_normals(seed, m, t0 + (uint32_t)n, ORA_TAG_O1, pid, d, z);
         for (int64_t i = 0; i < d; ++i) z[i] *= inv_sqrt_d;
         ora_O(d, 0.5 * eps, L, z, u);
+        round_f32(d, u);
         delta += phi_y(tg, sigma, integ, eps, y, u, g, logp, xb);
         ora_normals(seed, m, t0 + (uint32_t)n, ORA_TAG_O2, pid, d, z);
         for (int64_t i = 0; i < d; ++i) z[i] *= inv_sqrt_d;
         ora_O(d, 0.5 * eps, L, z, u);
+        round_f32(d, u);
     }
     int finite = isfinite(delta) && isfinite(*logp);
     for (int64_t i = 0; i < d && finite; ++i) finite = isfinite(y[i]) && isfinite(g[i]);
@@ -648,6 +666,7 @@ int ora_iterate(ora_state* s, ora_trace_row* row) {
     const int64_t M = s->M, d = s->d;
     const ora_config* c = &s->cfg;
     if (s->done) return 0;
+    g_round_f32 = c->round_state_f32;
     memset(row, 0, sizeof(*row));
     row->eevpd = row->eevpd_wanted = row->dtilde = row->max_delta = row->acc = NAN;
 
@@ -686,7 +705,9 @@ int ora_iterate(ora_state* s, ora_trace_row* row) {
         }
         /* Sec. 3.1 steps 2-5 */
         const double wanted = ora_F(c->C * dt);
-        if (nbad > 0 || !(eevpd > 0) || !isfinite(eevpd) || !isfinite(wanted))
+        if (c->fixed_eps > 0)
+            s->eps = c->fixed_eps;  /* the fixed-step ablation: no controller */
+        else if (nbad > 0 || !(eevpd > 0) || !isfinite(eevpd) || !isfinite(wanted))
             s->eps = 0.5 * s->eps;
         else
             s->eps = s->eps * pow(wanted / eevpd, 1.0 / 6.0);

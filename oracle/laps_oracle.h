@@ -104,6 +104,9 @@ typedef struct {
     int eevpd_centered;       /* 1: Var[Delta]/d (Eq. EEVPD); 0: mean Delta^2 / d */
     int adjusted;             /* 0: stop after the unadjusted phase */
     int force_switch_at;      /* >0: switch after this many unadjusted steps */
+    double fixed_eps;         /* >0: unadjusted step size held fixed (App. A, Fig. "stepsize") */
+    int round_state_f32;      /* 1: round y and u to binary32 after every map, to measure
+                                 how a binary32 chain state perturbs the run (not LAPS) */
 } ora_config;
 
 void ora_config_default(ora_config* c);

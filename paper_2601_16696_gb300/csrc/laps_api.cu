@@ -64,6 +64,12 @@ __global__ void unpack_rows_kernel(const float* __restrict__ src, const float* _
         dst[k] = (scale ? scale[i] : 1.0f) * src[m * d_pad + i];
     }
 }
+__global__ void ff_to_double_kernel(const float2* __restrict__ src, double* __restrict__ dst,
+                                    int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = (double)src[k].x + (double)src[k].y;
+}
 __global__ void fill_kernel(float* p, float v, int64_t n) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
@@ -96,11 +102,17 @@ static void coefs_table(Coefs& cf) {
 // ------------------------------------------------------------------ launch shape
 static const int kShapes[][2] = {{4, 4}, {8, 4}, {8, 8}, {16, 4}, {16, 8}, {32, 4}, {32, 8}, {32, 16}};
 
-static size_t resident_smem(int d_pad, int threads, int lpc, int d, int G) {
+// per-coordinate quantities reduced per shared-memory pass (all four when they fit)
+static int resident_qpp(int d_pad, int threads) {
+    const size_t per_q = (size_t)(threads / 32) * d_pad * sizeof(float);
+    int q = (int)std::min<size_t>(NQ, (64 * 1024) / std::max<size_t>(per_q, 1));
+    return std::max(1, q);
+}
+static size_t resident_smem(int d_pad, int threads, int lpc) {
     const int nwarps = threads / 32, slots = threads / lpc;
-    const int slice = (d + G - 1) / G + 1;
-    return (size_t)nwarps * d_pad * sizeof(float) + (size_t)slots * NCS * sizeof(double) +
-           (size_t)slice * NSL * sizeof(double);
+    const int qpp = resident_qpp(d_pad, threads);
+    return (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
+           (size_t)d_pad * sizeof(float) + (size_t)d_pad * sizeof(float4);
 }
 
 laps_status choose_shape(laps_ctx* c) {
@@ -125,15 +137,15 @@ laps_status choose_shape(laps_ctx* c) {
             if (threads < 32 || threads > kMaxThreads || threads % 32) continue;
             const int cpb = threads / lpc;
             const int G = (int)((c->M + cpb - 1) / cpb);
-            const size_t smem = resident_smem(c->d_pad, threads, lpc, c->d, G);
+            const size_t smem = resident_smem(c->d_pad, threads, lpc);
             if (smem > 200 * 1024) continue;
             CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int bps = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem));
             if ((long long)bps * nsm < G) continue;
-            // prefer the smallest per-lane footprint that keeps every chain resident,
-            // then more chains per block (fewer blocks in the barrier)
-            const double score = cpl * 1000.0 + (double)G / 1000.0;
+            // fewest blocks (one barrier arrival and one set of atomics per block),
+            // then the smallest per-lane footprint
+            const double score = (double)G * 100.0 + cpl;
             ok.push_back({lpc, cpl, threads, G, smem, score});
         }
     }
@@ -148,6 +160,7 @@ laps_status choose_shape(laps_ctx* c) {
     c->threads = best.threads;
     c->G = best.G;
     c->smem = best.smem;
+    c->qpp = resident_qpp(c->d_pad, best.threads);
     c->fn = resident_fn(kind, best.lpc, best.cpl);
     return LAPS_OK;
 }
@@ -168,35 +181,33 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.y = c->y;
     P.u = c->u;
     P.g = c->g;
-    P.logp = c->logp;
+    P.logp_ff = c->logp_ff;
     P.sigma = c->sigma;
     P.x0 = x0;
     P.x0_scale = x0_scale;
-    P.part_coord = c->part_coord;
-    P.part_chain = c->part_chain;
-    P.part_slice = c->part_slice;
+    P.acc = c->acc;
+    P.nacc = c->nacc;
+    P.ring = c->ring;
+    P.win_sums = c->win_sums;
     P.var_y = c->var_y;
-    P.win = c->win;
-    P.win_s1 = c->win_s1;
-    P.win_s2 = c->win_s2;
     P.Ex2 = c->have_truth ? c->Ex2 : nullptr;
-    P.Varx2 = c->have_truth ? c->Varx2 : nullptr;
+    P.inv_varx2 = c->inv_varx2;
     P.hyper = c->hyper;
     P.trace = c->trace;
     P.trace_cap = c->trace_cap;
     P.bar_count = c->bar;
-    P.bar_gen = c->bar + 1;
     P.status = c->status;
     const laps_config& g = c->cfg;
-    P.C = g.C;
-    P.alpha = g.alpha;
-    P.switch_tol = g.switch_tol;
-    P.acc_tol = g.acc_tol;
-    P.adj_L_factor = g.adj_L_factor;
-    P.eps0 = g.eps0_coef * std::sqrt((double)c->d);
-    P.a_target_mn2 = g.a_target_mn2;
-    P.a_target_mn4 = g.a_target_mn4;
-    P.stop_b2 = g.stop_b2;
+    P.C = (float)g.C;
+    P.alpha = (float)g.alpha;
+    P.switch_tol = (float)g.switch_tol;
+    P.acc_tol = (float)g.acc_tol;
+    P.adj_L_factor = (float)g.adj_L_factor;
+    P.eps0 = (float)(g.eps0_coef * std::sqrt((double)c->d));
+    P.a_target_mn2 = (float)g.a_target_mn2;
+    P.a_target_mn4 = (float)g.a_target_mn4;
+    P.stop_b2 = (float)g.stop_b2;
+    P.fixed_eps = (float)g.fixed_eps;
     P.stop_b2_max = g.stop_b2_max;
     P.T = c->T;
     P.n_total = g.n_total_steps;
@@ -212,9 +223,11 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.mode = mode;
     P.n_iters = n_iters;
     P.G = c->G;
+    P.qpp = c->qpp;
     P.bar_extra = g.barrier_extra_arrivals;
 
     CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->acc, 0, (size_t)3 * c->nacc * 4 * sizeof(unsigned long long), st));
     const Coefs* cf = c->coefs;
     void* args[] = {&P, &cf};
     CK(cudaLaunchCooperativeKernel(c->fn, dim3(c->G), dim3(c->threads), args, c->smem, st));
@@ -254,6 +267,7 @@ void laps_config_default(laps_config* c) {
     c->stop_b2_max = 0;
     c->precision = LAPS_FP32;
     c->barrier_timeout_ns = 2000000000LL;
+    c->fixed_eps = 0.0;
     c->chains_per_block = 0;
     c->lanes_per_chain = 0;
     c->coords_per_lane = 0;
@@ -326,16 +340,15 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
         c->allocs.push_back(*p);
         return true;
     };
+    c->nacc = NQ * c->d_pad + NCS;
     bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
-              alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp, M * 8) &&
+              alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp_ff, M * 8) &&
               alloc((void**)&c->sigma, c->d_pad * 4) &&
-              alloc((void**)&c->part_coord, (size_t)NQ * c->d_pad * c->G * 8) &&
-              alloc((void**)&c->part_chain, (size_t)NCS * c->G * 8) &&
-              alloc((void**)&c->part_slice, (size_t)NSL * c->G * 8) &&
-              alloc((void**)&c->var_y, c->d_pad * 8) &&
-              alloc((void**)&c->win, (size_t)c->T * c->d_pad * 8) &&
-              alloc((void**)&c->win_s1, c->d_pad * 8) && alloc((void**)&c->win_s2, c->d_pad * 8) &&
-              alloc((void**)&c->Ex2, c->d_pad * 8) && alloc((void**)&c->Varx2, c->d_pad * 8) &&
+              alloc((void**)&c->acc, (size_t)3 * c->nacc * 4 * 8) &&
+              alloc((void**)&c->var_y, c->d_pad * 4) &&
+              alloc((void**)&c->ring, (size_t)(c->T + 1) * c->d_pad * 8) &&
+              alloc((void**)&c->win_sums, (size_t)c->d_pad * 16) &&
+              alloc((void**)&c->Ex2, c->d_pad * 8) && alloc((void**)&c->inv_varx2, c->d_pad * 4) &&
               alloc((void**)&c->hyper, sizeof(Hyper)) &&
               alloc((void**)&c->trace, (size_t)c->trace_cap * sizeof(laps_trace_row)) &&
               alloc((void**)&c->bar, 4 * sizeof(unsigned)) && alloc((void**)&c->status, sizeof(int)) &&
@@ -365,14 +378,16 @@ void laps_destroy(laps_ctx* c) {
 
 laps_status laps_set_truth(laps_ctx* c, const double* Ex2, const double* Varx2) {
     if (!c || !Ex2 || !Varx2) return fail(LAPS_ERR_INVALID_ARG, "null argument");
-    std::vector<double> a(c->d_pad, 0.0), b(c->d_pad, 1.0);
+    std::vector<float2> a(c->d_pad, make_float2(0.0f, 0.0f));
+    std::vector<float> b(c->d_pad, 0.0f);
     for (int i = 0; i < c->d; ++i) {
         if (!(Varx2[i] > 0)) return fail(LAPS_ERR_INVALID_ARG, "Varx2 must be > 0");
-        a[i] = Ex2[i];
-        b[i] = Varx2[i];
+        const float hi = (float)Ex2[i];
+        a[i] = make_float2(hi, (float)(Ex2[i] - (double)hi));  // float-float copy of E_p[x^2]
+        b[i] = (float)(1.0 / Varx2[i]);
     }
     CK(cudaMemcpy(c->Ex2, a.data(), c->d_pad * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->Varx2, b.data(), c->d_pad * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->inv_varx2, b.data(), c->d_pad * 4, cudaMemcpyHostToDevice));
     c->have_truth = true;
     return LAPS_OK;
 }
@@ -396,10 +411,9 @@ laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t se
     h.b2_max = h.b2_avg = NAN;
     CK(cudaMemcpyAsync(c->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
-    CK(cudaMemsetAsync(c->win, 0, (size_t)c->T * c->d_pad * 8, st));
-    CK(cudaMemsetAsync(c->win_s1, 0, c->d_pad * 8, st));
-    CK(cudaMemsetAsync(c->win_s2, 0, c->d_pad * 8, st));
-    CK(cudaMemsetAsync(c->var_y, 0, c->d_pad * 8, st));
+    CK(cudaMemsetAsync(c->ring, 0, (size_t)(c->T + 1) * c->d_pad * 8, st));
+    CK(cudaMemsetAsync(c->win_sums, 0, (size_t)c->d_pad * 16, st));
+    CK(cudaMemsetAsync(c->var_y, 0, c->d_pad * 4, st));
     fill_kernel<<<grid_for(c->d_pad), 256, 0, st>>>(c->sigma, 1.0f, c->d_pad);
     CK(cudaGetLastError());
     // keep the caller's stream synchronous with the host copy of h above
@@ -452,7 +466,11 @@ laps_status laps_get_state(const laps_ctx* c, float* y, float* u, float* g, doub
                                                                  c->d, c->d_pad);
         CK(cudaGetLastError());
     }
-    if (logp) CK(cudaMemcpyAsync(logp, c->logp, c->M * 8, cudaMemcpyDeviceToDevice, st));
+    if (logp) {
+        if (!aligned(logp, 8)) return fail(LAPS_ERR_INVALID_ARG, "misaligned logp");
+        ff_to_double_kernel<<<grid_for(c->M), 256, 0, st>>>(c->logp_ff, logp, c->M);
+        CK(cudaGetLastError());
+    }
     if (sigma) CK(cudaMemcpyAsync(sigma, c->sigma, c->d * 4, cudaMemcpyDeviceToDevice, st));
     return LAPS_OK;
 }
@@ -462,6 +480,7 @@ static laps_status read_status(laps_ctx* c) {
     int s = 0;
     CK(cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
+    if (s == ST_NONFINITE) return fail(LAPS_ERR_NONFINITE, "non-finite initial position, log p or gradient");
     if (s != 0) return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
     return LAPS_OK;
 }
@@ -522,11 +541,11 @@ struct CkptHeader {
 static std::vector<std::pair<void*, size_t>> ckpt_buffers(laps_ctx* c) {
     const size_t Md = (size_t)c->M * c->d_pad;
     return {{c->y, Md * 4},           {c->u, Md * 4},          {c->g, Md * 4},
-            {c->logp, (size_t)c->M * 8}, {c->sigma, (size_t)c->d_pad * 4},
-            {c->var_y, (size_t)c->d_pad * 8},
-            {c->win, (size_t)c->T * c->d_pad * 8}, {c->win_s1, (size_t)c->d_pad * 8},
-            {c->win_s2, (size_t)c->d_pad * 8},   {c->Ex2, (size_t)c->d_pad * 8},
-            {c->Varx2, (size_t)c->d_pad * 8},    {c->hyper, sizeof(Hyper)},
+            {c->logp_ff, (size_t)c->M * 8}, {c->sigma, (size_t)c->d_pad * 4},
+            {c->var_y, (size_t)c->d_pad * 4},
+            {c->ring, (size_t)(c->T + 1) * c->d_pad * 8}, {c->win_sums, (size_t)c->d_pad * 16},
+            {c->Ex2, (size_t)c->d_pad * 8},    {c->inv_varx2, (size_t)c->d_pad * 4},
+            {c->hyper, sizeof(Hyper)},
             {c->trace, (size_t)c->trace_cap * sizeof(laps_trace_row)}};
 }
 

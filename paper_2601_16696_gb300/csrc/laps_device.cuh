@@ -11,7 +11,7 @@
 namespace laps {
 
 // ---------------------------------------------------------------- status codes
-enum : int { ST_OK = 0, ST_TIMEOUT = 4, ST_BADPARAM = 1 };
+enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5 };
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Ten rounds; each multiplies words 0 and 2 by the round multipliers, xors the
@@ -116,6 +116,73 @@ __device__ __forceinline__ double warp_max_d(double v) {
     return v;
 }
 
+// ---------------------------------------------------------------- fixed point
+// Exact, order-independent accumulation across blocks: a value is converted to
+// a 128-bit two's-complement integer with 64 fractional bits (|v| < 2^62,
+// resolution 2^-64), split into four 32-bit limbs, and each limb is added with
+// a 64-bit integer atomic into its own accumulator.  Integer addition commutes,
+// so the totals, and everything computed from them, are bit-identical from run
+// to run whatever order the blocks arrive in.
+struct i128 {
+    unsigned long long lo;
+    long long hi;
+};
+__device__ __forceinline__ i128 f32_to_fx(float f, int& bad) {
+    i128 r{0ull, 0ll};
+    const unsigned b = __float_as_uint(f);
+    const int e = (b >> 23) & 0xff;
+    if (e == 0) return r;  // zero or subnormal: below the resolution
+    if (e == 0xff) { bad = 1; return r; }
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // |f| = m 2^(e-150)
+    const int sh = e - 150 + 64;  // bit position of m's lsb in |f| 2^64
+    if (sh < 0) {
+        if (sh > -24) r.lo = m >> (-sh);
+    } else if (sh < 64) {
+        r.lo = m << sh;
+        r.hi = (sh > 40) ? (long long)(m >> (64 - sh)) : 0ll;
+    } else if (sh < 64 + 38) {
+        r.hi = (long long)(m << (sh - 64));
+    } else {
+        bad = 1;
+        return r;
+    }
+    if (b >> 31) {  // two's-complement negation
+        r.lo = ~r.lo + 1ull;
+        r.hi = ~r.hi + (r.lo == 0ull ? 1ll : 0ll);
+    }
+    return r;
+}
+__device__ __forceinline__ i128 fx_add(i128 a, i128 b) {
+    i128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ll : 0ll);
+    return r;
+}
+// acc: four u64 limb accumulators of one quantity
+__device__ __forceinline__ void fx_atomic_add(unsigned long long* acc, ff v, int& bad) {
+    const i128 x = fx_add(f32_to_fx(v.hi, bad), f32_to_fx(v.lo, bad));
+    atomicAdd(acc + 0, x.lo & 0xffffffffull);
+    atomicAdd(acc + 1, x.lo >> 32);
+    atomicAdd(acc + 2, (unsigned long long)x.hi & 0xffffffffull);
+    atomicAdd(acc + 3, (unsigned long long)(x.hi >> 32));  // arithmetic shift: signed limb
+}
+// total of the four limb sums as a float-float (no FP64 arithmetic)
+__device__ __forceinline__ ff fx_read(const unsigned long long* acc) {
+    const unsigned long long a0 = __ldcg(acc + 0), a1 = __ldcg(acc + 1), a2 = __ldcg(acc + 2);
+    const long long a3 = (long long)__ldcg(acc + 3);
+    const unsigned long long t0 = a0;
+    const unsigned long long t1 = a1 + (t0 >> 32);
+    const unsigned long long t2 = a2 + (t1 >> 32);
+    const long long t3 = a3 + (long long)(t2 >> 32);
+    const unsigned long long lo = (t0 & 0xffffffffull) | (t1 << 32);
+    const long long hi = (long long)((t2 & 0xffffffffull) | ((unsigned long long)t3 << 32));
+    const float fh = __ll2float_rn(hi);                 // integer part, rounded
+    const long long rest = hi - __float2ll_rn(fh);      // exact remainder of the integer part
+    const float fl = __ll2float_rn(rest) + __ull2float_rn(lo) * 5.421010862427522e-20f;  // 2^-64
+    const float s = fh + fl;
+    return ff{s, fl - (s - fh)};
+}
+
 // ---------------------------------------------------------------- timers, barrier
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -132,6 +199,40 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid-wide barrier on a monotone arrival counter (reset to 0 before the
+// launch): barrier number k (k = 1, 2, ...) waits until the counter reaches
+// k * expected.  One atomic per block and a polling read; no reset between
+// barriers.  Bounded exactly like grid_barrier below.
+__device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, unsigned target,
+                                                long long timeout_ns) {
+    __shared__ int s_ok2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+        if (ld_acquire_u32(count) < target) {
+            const uint64_t t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(count) < target) {
+                if ((++spins & 31u) == 0u) {
+                    if (ld_volatile_i32(status) != ST_OK) { ok = 0; break; }
+                    if ((long long)(global_ns() - t0) > timeout_ns) {
+                        atomicCAS(status, ST_OK, ST_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (ok && ld_volatile_i32(status) != ST_OK) ok = 0;
+        s_ok2 = ok;
+    }
+    __syncthreads();
+    return s_ok2 != 0;
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The

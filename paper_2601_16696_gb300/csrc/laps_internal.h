@@ -21,10 +21,15 @@ struct laps_ctx {
     int d = 0, d_pad = 0, T = 0, trace_cap = 0;
     // ensemble state (sampler coordinates, [M][d_pad]) and phase machine
     float *y = nullptr, *u = nullptr, *g = nullptr, *sigma = nullptr;
-    double* logp = nullptr;
-    double *part_coord = nullptr, *part_chain = nullptr, *part_slice = nullptr;
-    double *var_y = nullptr, *win = nullptr, *win_s1 = nullptr, *win_s2 = nullptr;
-    double *Ex2 = nullptr, *Varx2 = nullptr;
+    float2* logp_ff = nullptr;
+    unsigned long long* acc = nullptr;
+    int nacc = 0;
+    float2* ring = nullptr;
+    float4* win_sums = nullptr;
+    float* var_y = nullptr;
+    float2* Ex2 = nullptr;
+    float* inv_varx2 = nullptr;
+    int qpp = 1;
     laps::Hyper* hyper = nullptr;
     laps_trace_row* trace = nullptr;
     unsigned* bar = nullptr;

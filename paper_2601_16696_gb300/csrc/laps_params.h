@@ -1,6 +1,8 @@
 // laps_params.h -- parameter and state blocks shared by the host API and the
-// kernels (plain structs, no CUDA types, included by .cu and .cpp files).
+// kernels (plain structs, no CUDA types beyond the vector types).
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 #include "../../include/laps.h"
@@ -9,23 +11,23 @@ namespace laps {
 
 // Hyperparameters and phase machine of Alg. 1 (identical in every block).
 struct Hyper {
-    double eps, L, lo, hi, a_target;
-    double eps_used;
-    double eevpd, eevpd_wanted, dtilde, max_delta, acc, b2_max, b2_avg, sum_var;
+    float eps, L, lo, hi, a_target, eps_used;
+    float eevpd, eevpd_wanted, dtilde, max_delta, acc, b2_max, b2_avg, sum_var;
     double b2_first_ns;
     long long grads, b2_first_grads;
     unsigned long long t0_ns;
     int phase, t, t_switch, integ, adapting, p, done, iters, win_n, nonfinite_total;
-    int nonfinite_last, b2_first_t, pad_[2];
+    int nonfinite_last, b2_first_t;
 };
 
 enum : int { TGT_GAUSS = 0, TGT_BANANA = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3 };
 enum : int { INTEG_LF = 0, INTEG_MN2 = 1, INTEG_MN4 = 2 };
 enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4 };
 
-// per-coordinate sums kept per block, and per-chain / per-slice scalars
-enum : int { NQ = 4 };                                   // sum y, y^2, g, y g
+// per-coordinate sums (y, y^2, g, y g) and per-chain sums kept per iteration
+enum : int { NQ = 4 };
 enum : int { CS_DSUM = 0, CS_DSQ, CS_NFIN, CS_NBAD, CS_ASUM, NCS };
+enum : int { NCSF = 6 };  // floats per chain slot in shared memory (Delta as hi, lo)
 enum : int { SL_VAR = 0, SL_DV, SL_MAXDEL, SL_B2SUM, SL_B2MAX, NSL };
 
 struct KParams {
@@ -37,36 +39,34 @@ struct KParams {
     const float* prec;  // gauss: [d_pad], zero padded
     // ensemble state, sampler coordinates, [M][d_pad]
     float *y, *u, *g;
-    double* logp;       // [M]
+    float2* logp_ff;    // [M] log p as float-float
     float* sigma;       // [d_pad] preconditioner (1 before the switch)
     const float* x0;    // init: [M][d] caller layout, or nullptr for Philox
     float x0_scale;
-    // scratch (global)
-    double* part_coord;  // [NQ][d_pad][G]
-    double* part_chain;  // [NCS][G]
-    double* part_slice;  // [NSL][G]
-    double* var_y;       // [d_pad] ensemble variance of the last iteration
-    double* win;         // [T][d_pad] E[x_i^2] ring
-    double* win_s1;      // [d_pad] running window sum
-    double* win_s2;      // [d_pad] running window sum of squares
-    const double* Ex2;   // [d_pad] truth or nullptr
-    const double* Varx2;
+    // reduction and window state (global)
+    unsigned long long* acc;  // [3][nacc][4] fixed-point limb accumulators
+    int nacc;                 // NQ * d_pad + NCS
+    float2* ring;             // [T + 1][d_pad] window values E[x_i^2] (float-float)
+    float4* win_sums;         // [d_pad] running window sums (s1, s2 as float-float)
+    float* var_y;             // [d_pad] ensemble variance of the last iteration
+    const float2* Ex2;        // [d_pad] truth E_p[x_i^2] (float-float) or nullptr
+    const float* inv_varx2;   // [d_pad] 1 / Var_p[x_i^2]
     Hyper* hyper;
     laps_trace_row* trace;
     int trace_cap;
     unsigned* bar_count;
-    unsigned* bar_gen;
     int* status;
     // configuration
-    double C, alpha, switch_tol, acc_tol, adj_L_factor, eps0, a_target_mn2, a_target_mn4;
-    double stop_b2;
+    float C, alpha, switch_tol, acc_tol, adj_L_factor, eps0, a_target_mn2, a_target_mn4;
+    float stop_b2, fixed_eps;
     int stop_b2_max;
     int T, n_total, N, mn4_min_dim, eevpd_centered, adjusted, force_switch_at;
     long long timeout_ns;
     uint32_t seed_lo, seed_hi, pid;
-    int mode;     // 0: initialise, 1: iterate
-    int n_iters;  // iterations of this launch
-    int G;        // blocks in the grid
+    int mode;       // 0: initialise, 1: iterate
+    int n_iters;    // iterations of this launch
+    int G;          // blocks in the grid
+    int qpp;        // per-coordinate quantities reduced per shared-memory pass
     int bar_extra;  // extra arrivals every barrier waits for (test hook; 0 normally)
 };
 

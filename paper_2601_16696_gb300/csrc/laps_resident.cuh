@@ -7,17 +7,17 @@
 //   1. the chain update: an unadjusted step O_{eps/2} Phi_eps O_{eps/2} with
 //      leapfrog (App. E, Eq. "discrete update"), or a MAMS proposal of N such
 //      steps with MN2/MN4 and the accept/reject test (App. F);
-//   2. per-block sums of y, y^2, g, y g over the block's chains (compensated
-//      FP32) and of the per-chain energy error / acceptance, written as FP64
-//      block partials (Eq. ECA);
-//   3. grid barrier; block b reduces the partials of its slice of coordinates
-//      over all blocks in FP64, in block order, and derives Var, V_ii (App. B),
-//      the window statistic delta[x_i^2] (Eq. "relative fluctuations") and
-//      b^2 (Eq. "bias") for those coordinates;
-//   4. grid barrier; every block reduces the slice scalars in the same order
-//      and runs the same FP64 finalise (Sec. 3.1 controller, Eq. "L", the
-//      switch of Sec. 4, the bisection of Sec. 5.1), so all blocks hold
-//      bit-identical hyperparameters without a broadcast.
+//   2. per-block sums of y, y^2, g, y g over the block's chains and of the
+//      per-chain energy error / acceptance (compensated FP32), added into
+//      global 128-bit fixed-point accumulators with integer atomics (exact,
+//      so the totals do not depend on the order of the blocks);
+//   3. one grid barrier;
+//   4. every block reads the totals (Eq. ECA) and computes, identically, the
+//      per-coordinate Var, V_ii (App. B), the window statistic
+//      delta[x_i^2] (Eq. "relative fluctuations"), b^2 (Eq. "bias") and the
+//      finalise (Sec. 3.1 controller, Eq. "L", the switch of Sec. 4, the
+//      bisection of Sec. 5.1), so all blocks hold bit-identical
+//      hyperparameters without a broadcast or a second barrier.
 #pragma once
 #include <cmath>
 
@@ -245,13 +245,56 @@ __device__ __forceinline__ void phi_step(const KParams& P, const Coefs& cf, int 
 __device__ __forceinline__ bool finite_f(float v) { return isfinite(v); }
 
 // FP32 scalars of the next iteration: eps, and the O-map constants for a half
-// step, c1 = exp(-(eps/2)/L), c2 = sqrt(1 - c1^2) scaled by 1/sqrt(d).
+// step, c1 = exp(-(eps/2)/L), c2 = sqrt(1 - c1^2) = sqrt(-expm1(-eps/L)), the
+// latter scaled by 1/sqrt(d).
 __device__ __forceinline__ void set_step_scalars(const Hyper& H, int d, float& eps, float& c1,
                                                  float& c2s) {
-    eps = (float)H.eps;
-    const double e = exp(-0.5 * H.eps / H.L);
-    c1 = (float)e;
-    c2s = (float)(sqrt(1.0 - e * e) / sqrt((double)d));
+    eps = H.eps;
+    c1 = expf(-0.5f * H.eps / H.L);
+    c2s = sqrtf(-expm1f(-H.eps / H.L)) / sqrtf((float)d);
+}
+
+// ---------------------------------------------------------------- float-float helpers
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
+    const float s = p + e;
+    return ff{s, e - (s - p)};
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) { return ff_mul(a, ff{b, 0.0f}); }
+__device__ __forceinline__ ff ff_divf(ff a, float b) {
+    const float q1 = a.hi / b;
+    const ff r = ff_add(a, ff_neg(ff_mulf(ff{q1, 0.0f}, b)));
+    const float q2 = r.hi / b;
+    const float s = q1 + q2;
+    return ff{s, q2 - (s - q1)};
+}
+__device__ __forceinline__ float ff_f(ff a) { return a.hi + a.lo; }
+
+// block-wide reductions in a fixed order (identical in every block)
+__device__ __forceinline__ ff block_sum_ff(ff v, ff* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = group_sum_ff<32>(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    ff s = ff_make(0.0f);
+    for (int w = 0; w < nw; ++w) s = ff_add(s, sh[w]);
+    return s;
+}
+__device__ __forceinline__ float block_max(float v, float* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (w > v || w != w) ? w : v;
+    }
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float s = 0.0f;
+    for (int w = 0; w < nw; ++w) s = (sh[w] > s || sh[w] != sh[w]) ? sh[w] : s;
+    return s;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -263,9 +306,12 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Hyper H;
     __shared__ Coefs CF;
-    __shared__ double s_fin[NCS + NSL];
-    __shared__ int s_switch;
-    __shared__ float s_eps, s_c1, s_c2s;  // step scalars of the next iteration (FP32)
+    __shared__ ff s_red[kMaxThreads / 32];
+    __shared__ float s_redf[kMaxThreads / 32];
+    __shared__ ff s_tot[NCS];
+    __shared__ ff s_sl[NSL];
+    __shared__ int s_switch, s_bad;
+    __shared__ float s_eps, s_c1, s_c2s;  // step scalars of the next iteration
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -276,19 +322,26 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     const bool active = m < P.M;
     const int dp = P.d_pad;
     const unsigned gmask = ((LPC == 32) ? 0xffffffffu : ((1u << LPC) - 1u)) << (grp * LPC);
+    const size_t acc_set = (size_t)P.nacc * 4;  // u64 limbs per accumulator set
 
-    float* sq = reinterpret_cast<float*>(smem_raw);                      // [nwarps][d_pad]
-    double* s_cs = reinterpret_cast<double*>(sq + (size_t)nwarps * dp);  // [slots][NCS]
-    const int i0 = (int)(((long long)blockIdx.x * P.d) / G);
-    const int i1 = (int)(((long long)(blockIdx.x + 1) * P.d) / G);
-    double* s_sl = s_cs + (size_t)slots * NCS;                           // [i1-i0][NSL]
+    // dynamic shared memory: per-warp column sums, per-chain scalars,
+    // per-coordinate variance (for the switch), window sums
+    float* sq = reinterpret_cast<float*>(smem_raw);                        // [qpp][nwarps][dp]
+    float* s_cs = sq + (size_t)P.qpp * nwarps * dp;                         // [slots][NCSF]
+    float* s_var = s_cs + (size_t)slots * NCSF;                             // [dp]
+    float4* s_win = reinterpret_cast<float4*>(s_var + dp);                  // [dp] (s1, s2 as ff)
 
     if (tid == 0) {
         H = *P.hyper;
         set_step_scalars(H, P.d, s_eps, s_c1, s_c2s);
+        s_bad = 0;
     }
     for (int i = tid; i < (int)(sizeof(Coefs) / 4); i += blockDim.x)
         reinterpret_cast<int*>(&CF)[i] = reinterpret_cast<const int*>(coefs)[i];
+    for (int i = tid; i < dp; i += blockDim.x) {
+        s_win[i] = P.win_sums[i];
+        s_var[i] = 0.0f;
+    }
     __syncthreads();
 
     // ---- registers: state and per-coordinate constants
@@ -316,9 +369,8 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         pr[4 * k] = p.x; pr[4 * k + 1] = p.y; pr[4 * k + 2] = p.z; pr[4 * k + 3] = p.w;
     }
     if (P.mode == 1 && active) {
-        const double l = P.logp[m];
-        lp.hi = (float)l;
-        lp.lo = (float)(l - (double)lp.hi);
+        const float2 l = P.logp_ff[m];
+        lp = ff{l.x, l.y};
     }
 
     // ---- initialisation (Alg. 1 first lines, App. C "Initialization")
@@ -352,14 +404,19 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
 #pragma unroll
             for (int q = 0; q < CPL; ++q) u[q] = g[q] * inv;
         }
+        // a non-finite initial point would poison every ensemble statistic: report it
+        bool bad = active && !isfinite(lp.hi);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) bad = bad || (active && !(finite_f(y[q]) && finite_f(g[q])));
+        if (bad) atomicCAS(P.status, ST_OK, ST_NONFINITE);
     }
 
     const int n_iter = (P.mode == 0) ? 1 : P.n_iters;
-
     for (int it = 0; it < n_iter; ++it) {
         if (P.mode == 1 && H.done) break;
         // ------------------------------------------------ 1. chain update
-        double c_d = 0.0, c_d2 = 0.0, c_fin = 0.0, c_bad = 0.0, c_a = 0.0;
+        ff c_d = ff_make(0.0f);
+        float c_d2 = 0.0f, c_fin = 0.0f, c_bad = 0.0f, c_a = 0.0f;
         if (P.mode == 1) {
             const float eps = s_eps, c1 = s_c1, c2s = s_c2s;
             float y0[CPL], g0[CPL], u0[CPL];
@@ -414,8 +471,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 const uint4 r = philox4x32_10(
                     make_uint4(0u, (uint32_t)m, (uint32_t)H.p, TAG_MH | (P.pid << 8)), P.seed_lo,
                     P.seed_hi);
-                const float logU = logf(u01(r.x));
-                const ff s = ff_add(dl, logU);
+                const ff s = ff_add(dl, logf(u01(r.x)));
                 keep = !bad && (s.hi < 0.0f || (s.hi == 0.0f && s.lo < 0.0f));
                 a_m = bad ? 0.0f : (dl.hi <= 0.0f ? 1.0f : expf(-(dl.hi + dl.lo)));
             }
@@ -424,175 +480,189 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 for (int q = 0; q < CPL; ++q) { y[q] = y0[q]; g[q] = g0[q]; u[q] = u0[q]; }
                 lp = lp0;
             }
-            if (active && gl == 0) {  // one lane per chain does the FP64 bookkeeping
+            if (active) {
                 if (H.phase == 0) {
-                    if (bad) c_bad = 1.0;
-                    else {
-                        const double dd = ff_to_double(dl);
-                        c_d = dd; c_d2 = dd * dd; c_fin = 1.0;
-                    }
+                    if (bad) c_bad = 1.0f;
+                    else { c_d = dl; c_d2 = ff_f(dl) * ff_f(dl); c_fin = 1.0f; }
                 } else {
                     c_a = a_m;
-                    c_bad = bad ? 1.0 : 0.0;
+                    c_bad = bad ? 1.0f : 0.0f;
                 }
             }
         }
-        // ------------------------------------------------ 2. block partials
-        for (int qd = 0; qd < NQ; ++qd) {
-            if (H.phase == 1 && P.mode == 1 && qd >= 2) break;  // g sums unused after the switch
+        // ------------------------------------------------ 2. block sums -> fixed-point totals
+        unsigned long long* acc = P.acc + (size_t)(it % 3) * acc_set;
+        {   // clear this block's share of the set the next iteration adds into
+            unsigned long long* nxt = P.acc + (size_t)((it + 1) % 3) * acc_set;
+            const size_t per = (acc_set + G - 1) / G;
+            const size_t b0 = (size_t)blockIdx.x * per, b1 = min(acc_set, b0 + per);
+            for (size_t k = b0 + tid; k < b1; k += blockDim.x) nxt[k] = 0ull;
+        }
+        const int nq = (H.phase == 1 && P.mode == 1) ? 2 : NQ;  // g sums unused after the switch
+        int fx_bad = 0;
+        for (int q0 = 0; q0 < nq; q0 += P.qpp) {
+            const int q1 = min(nq, q0 + P.qpp);
+            for (int qd = q0; qd < q1; ++qd) {
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
+                for (int k = 0; k < NB; ++k) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int q = 4 * k + c;
-                    float v = qd == 0 ? y[q] : qd == 1 ? y[q] * y[q] : qd == 2 ? g[q] : y[q] * g[q];
-                    v = active ? v : 0.0f;
-                    v = across_groups<LPC>(v);
-                    const int j = gl + LPC * k;
-                    if (grp == 0 && j < P.nblk) sq[warp * dp + 4 * j + c] = v;
+                    for (int c = 0; c < 4; ++c) {
+                        const int q = 4 * k + c;
+                        float v = qd == 0 ? y[q] : qd == 1 ? y[q] * y[q] : qd == 2 ? g[q] : y[q] * g[q];
+                        v = active ? v : 0.0f;
+                        v = across_groups<LPC>(v);
+                        const int j = gl + LPC * k;
+                        if (grp == 0 && j < P.nblk) sq[((size_t)(qd - q0) * nwarps + warp) * dp + 4 * j + c] = v;
+                    }
                 }
             }
             __syncthreads();
-            for (int col = tid; col < dp; col += blockDim.x) {
+            for (int col = tid; col < (q1 - q0) * dp; col += blockDim.x) {
+                const int qd = q0 + col / dp, i = col - (col / dp) * dp;
+                if (i >= P.d) continue;
                 ff s = ff_make(0.0f);
-                for (int w = 0; w < nwarps; ++w) s = ff_add(s, sq[w * dp + col]);
-                P.part_coord[((size_t)qd * dp + col) * G + blockIdx.x] = ff_to_double(s);
+                const float* src = sq + (size_t)(qd - q0) * nwarps * dp + i;
+                for (int w = 0; w < nwarps; ++w) s = ff_add(s, src[(size_t)w * dp]);
+                fx_atomic_add(acc + ((size_t)qd * dp + i) * 4, s, fx_bad);
             }
             __syncthreads();
         }
         if (gl == 0) {
-            double* cs = s_cs + (size_t)slot * NCS;
-            cs[CS_DSUM] = c_d; cs[CS_DSQ] = c_d2; cs[CS_NFIN] = c_fin; cs[CS_NBAD] = c_bad;
-            cs[CS_ASUM] = c_a;
+            float* cs = s_cs + (size_t)slot * NCSF;
+            cs[0] = c_d.hi; cs[1] = c_d.lo; cs[2] = c_d2; cs[3] = c_fin; cs[4] = c_bad; cs[5] = c_a;
         }
         __syncthreads();
         if (tid < NCS) {
-            double s = 0.0;
-            for (int sl = 0; sl < slots; ++sl) s += s_cs[(size_t)sl * NCS + tid];
-            P.part_chain[(size_t)tid * G + blockIdx.x] = s;
+            ff s = ff_make(0.0f);
+            for (int sl = 0; sl < slots; ++sl) {
+                const float* cs = s_cs + (size_t)sl * NCSF;
+                if (tid == CS_DSUM) s = ff_add(s, ff{cs[0], cs[1]});
+                else s = ff_add(s, cs[tid + 1]);
+            }
+            fx_atomic_add(acc + ((size_t)NQ * dp + tid) * 4, s, fx_bad);
         }
-        // ------------------------------------------------ 3. slice reduction
-        if (!grid_barrier(P.bar_count, P.bar_gen, P.status, G + P.bar_extra, P.timeout_ns)) return;
+        if (fx_bad) atomicOr(&s_bad, 1);
+        // ------------------------------------------------ 3. the one grid barrier
+        if (!grid_sync_count(P.bar_count, P.status, (unsigned)(it + 1) * (unsigned)(G + P.bar_extra),
+                             P.timeout_ns))
+            return;
+        // ------------------------------------------------ 4. statistics (every block)
         const bool push = (P.mode == 1 && H.phase == 0);
-        const bool have_g = !(P.mode == 1 && H.phase == 1);
-        for (int i = i0 + warp; i < i1; i += nwarps) {
-            double s[NQ];
-#pragma unroll
-            for (int qd = 0; qd < NQ; ++qd) {
-                double a = 0.0;
-                if (qd < 2 || have_g)
-                    for (int c = lane; c < G; c += 32)
-                        a += __ldcg(&P.part_coord[((size_t)qd * dp + i) * G + c]);
-                s[qd] = warp_sum_d(a);
+        const bool have_g = nq == NQ;
+        const float iM = 1.0f / (float)P.M;
+        const int win_n = H.win_n;
+        const int slot_new = win_n % (P.T + 1), slot_old = (win_n + 1) % (P.T + 1);
+        ff a_var = ff_make(0.0f), a_dv = ff_make(0.0f), a_b2 = ff_make(0.0f);
+        float a_del = 0.0f, a_b2m = 0.0f;
+        for (int i = tid; i < P.d; i += blockDim.x) {
+            const ff sy = fx_read(acc + ((size_t)0 * dp + i) * 4);
+            const ff syy = fx_read(acc + ((size_t)1 * dp + i) * 4);
+            const ff mean = ff_mulf(sy, iM), ey2 = ff_mulf(syy, iM);
+            const float var_y = ff_f(ff_add(ey2, ff_neg(ff_mul(mean, mean))));
+            const float sgi = P.sigma[i];
+            const float s2i = sgi * sgi;
+            const ff ex2 = ff_mulf(ey2, s2i);
+            a_var = ff_add(a_var, s2i * var_y);
+            s_var[i] = var_y;
+            if (have_g) {
+                const ff sg_ = fx_read(acc + ((size_t)2 * dp + i) * 4);
+                const ff syg = fx_read(acc + ((size_t)3 * dp + i) * 4);
+                // V_ii = -(E[y g] - E[y] E[g])  (App. B, Eq. ECA)
+                const float V = -ff_f(ff_add(ff_mulf(syg, iM), ff_neg(ff_mul(mean, ff_mulf(sg_, iM)))));
+                a_dv = ff_add(a_dv, (1.0f - V) * (1.0f - V));
             }
-            if (lane == 0) {
-                const double iM = 1.0 / (double)P.M;
-                const double mean = s[0] * iM, ey2 = s[1] * iM;
-                const double var_y = ey2 - mean * mean;
-                const double sgi = (double)P.sigma[i];
-                const double var_x = sgi * sgi * var_y, ex2 = sgi * sgi * ey2;
-                const double V = -(s[3] * iM - mean * (s[2] * iM));
-                double del = 0.0;
-                if (push) {
-                    const int slotw = H.win_n % P.T;
-                    const bool full = H.win_n >= P.T;
-                    double* w = P.win + (size_t)slotw * dp + i;
-                    const double old = full ? *w : 0.0;
-                    *w = ex2;
-                    const double s1 = P.win_s1[i] + ex2 - old;
-                    const double s2 = P.win_s2[i] + ex2 * ex2 - old * old;
-                    P.win_s1[i] = s1;
-                    P.win_s2[i] = s2;
-                    if (H.win_n + 1 >= P.T) {
-                        const double mu = s1 / P.T;
-                        const double vv = (s2 - s1 * s1 / P.T) / (P.T - 1);
-                        del = sqrt(vv > 0.0 ? vv : 0.0) / mu;
-                    }
+            if (push) {
+                // moving window of E[x_i^2]: running sums over the last T values
+                float4 w = s_win[i];
+                ff s1{w.x, w.y}, s2{w.z, w.w};
+                if (win_n >= P.T) {
+                    const float2 o = __ldcg(reinterpret_cast<const float2*>(P.ring) + (size_t)slot_old * dp + i);
+                    const ff old{o.x, o.y};
+                    s1 = ff_add(s1, ff_neg(old));
+                    s2 = ff_add(s2, ff_neg(ff_mul(old, old)));
                 }
-                double b2 = 0.0;
-                if (P.Ex2) {
-                    const double e = ex2 - P.Ex2[i];
-                    b2 = e * e / P.Varx2[i];
+                s1 = ff_add(s1, ex2);
+                s2 = ff_add(s2, ff_mul(ex2, ex2));
+                s_win[i] = make_float4(s1.hi, s1.lo, s2.hi, s2.lo);
+                if (blockIdx.x == 0) P.ring[(size_t)slot_new * dp + i] = make_float2(ex2.hi, ex2.lo);
+                if (win_n + 1 >= P.T) {
+                    const float Tf = (float)P.T;
+                    const ff mu = ff_divf(s1, Tf);
+                    const float vv = ff_f(ff_add(s2, ff_neg(ff_mul(s1, mu)))) / (Tf - 1.0f);
+                    const float del = sqrtf(vv > 0.0f ? vv : 0.0f) / ff_f(mu);
+                    a_del = (del > a_del || del != del) ? del : a_del;
                 }
-                P.var_y[i] = var_y;
-                double* o = s_sl + (size_t)(i - i0) * NSL;
-                o[SL_VAR] = var_x;
-                o[SL_DV] = (1.0 - V) * (1.0 - V);
-                o[SL_MAXDEL] = del;
-                o[SL_B2SUM] = b2;
-                o[SL_B2MAX] = b2;
+            }
+            if (P.Ex2) {
+                const float2 e = P.Ex2[i];
+                const float dd = ff_f(ff_add(ex2, ff_neg(ff{e.x, e.y})));
+                const float b2 = dd * dd * P.inv_varx2[i];
+                a_b2 = ff_add(a_b2, b2);
+                a_b2m = (b2 > a_b2m || b2 != b2) ? b2 : a_b2m;
             }
         }
+        {
+            const ff v0 = block_sum_ff(a_var, s_red);
+            const ff v1 = block_sum_ff(a_dv, s_red);
+            const ff v3 = block_sum_ff(a_b2, s_red);
+            const float v2 = block_max(a_del, s_redf);
+            const float v4 = block_max(a_b2m, s_redf);
+            if (tid == 0) {
+                s_sl[SL_VAR] = v0; s_sl[SL_DV] = v1; s_sl[SL_B2SUM] = v3;
+                s_sl[SL_MAXDEL] = ff_make(v2); s_sl[SL_B2MAX] = ff_make(v4);
+            }
+        }
+        if (tid < NCS) s_tot[tid] = fx_read(acc + ((size_t)NQ * dp + tid) * 4);
         __syncthreads();
-        if (tid < NSL) {
-            double a = 0.0;  // sums start at 0; maxima too (all terms are >= 0)
-            for (int i = i0; i < i1; ++i) {
-                const double v = s_sl[(size_t)(i - i0) * NSL + tid];
-                if (tid == SL_MAXDEL || tid == SL_B2MAX) a = (v > a || v != v) ? v : a;
-                else a += v;
-            }
-            P.part_slice[(size_t)tid * G + blockIdx.x] = a;
-        }
-        // ------------------------------------------------ 4. finalise
-        if (!grid_barrier(P.bar_count, P.bar_gen, P.status, G + P.bar_extra, P.timeout_ns)) return;
-        for (int col = warp; col < NCS + NSL; col += nwarps) {
-            const double* src = col < NCS ? P.part_chain + (size_t)col * G
-                                          : P.part_slice + (size_t)(col - NCS) * G;
-            const bool is_max = (col == NCS + SL_MAXDEL) || (col == NCS + SL_B2MAX);
-            double a = 0.0;
-            for (int c = lane; c < G; c += 32) {
-                const double v = __ldcg(src + c);
-                a = is_max ? ((v > a || v != v) ? v : a) : a + v;
-            }
-            s_fin[col] = is_max ? warp_max_d(a) : warp_sum_d(a);
-        }
-        __syncthreads();
+        // ------------------------------------------------ 5. finalise (identical in every block)
         if (tid == 0) {
-            const double d = (double)P.d;
-            const double sum_var = s_fin[NCS + SL_VAR];
+            const float d = (float)P.d;
+            const float sum_var = ff_f(s_sl[SL_VAR]);
             s_switch = 0;
             if (P.mode == 0) {
-                H.eps = P.eps0;
-                H.L = P.alpha * sqrt(sum_var);
+                H.eps = P.fixed_eps > 0.0f ? P.fixed_eps : P.eps0;
+                H.L = P.alpha * sqrtf(sum_var);
                 H.t0_ns = global_ns();
             } else if (H.phase == 0) {
                 // Sec. 3.1: EEVPD, D~, desired EEVPD, new step size; Eq. "L"
-                const double nfin = s_fin[CS_NFIN], nbad = s_fin[CS_NBAD];
-                double eevpd = NAN;
-                if (nfin > 0) {
-                    const double mean = s_fin[CS_DSUM] / nfin;
-                    const double sq2 = s_fin[CS_DSQ] / nfin;
-                    eevpd = (P.eevpd_centered ? sq2 - mean * mean : sq2) / d;
+                const float nfin = ff_f(s_tot[CS_NFIN]), nbad = ff_f(s_tot[CS_NBAD]);
+                float eevpd = NAN;
+                if (nfin > 0.0f) {
+                    const ff mean = ff_divf(s_tot[CS_DSUM], nfin);
+                    const ff sq2 = ff_divf(s_tot[CS_DSQ], nfin);
+                    eevpd = ff_f(P.eevpd_centered ? ff_add(sq2, ff_neg(ff_mul(mean, mean))) : sq2) / d;
                 }
-                const double D = s_fin[NCS + SL_DV] / d;
-                const double cd = P.C * D, rt = sqrt(cd);
-                const double wanted = 4.0 * cd * rt / ((1.0 + rt) * (1.0 + rt));
+                const float D = ff_f(s_sl[SL_DV]) / d;
+                const float cd = P.C * D, rt = sqrtf(cd);
+                const float wanted = 4.0f * cd * rt / ((1.0f + rt) * (1.0f + rt));
                 H.eps_used = H.eps;
-                if (nbad > 0 || !(eevpd > 0) || !isfinite(eevpd) || !isfinite(wanted))
-                    H.eps = 0.5 * H.eps;
+                if (P.fixed_eps > 0.0f)
+                    H.eps = P.fixed_eps;
+                else if (nbad > 0.0f || !(eevpd > 0.0f) || !isfinite(eevpd) || !isfinite(wanted))
+                    H.eps = 0.5f * H.eps;
                 else
-                    H.eps = H.eps * pow(wanted / eevpd, 1.0 / 6.0);
-                H.L = P.alpha * sqrt(sum_var);
+                    H.eps = H.eps * powf(wanted / eevpd, 1.0f / 6.0f);
+                H.L = P.alpha * sqrtf(sum_var);
                 H.t += 1;
                 H.grads += 1;
                 H.win_n += 1;
                 H.eevpd = eevpd;
                 H.eevpd_wanted = wanted;
                 H.dtilde = D;
-                H.max_delta = (H.win_n >= P.T) ? s_fin[NCS + SL_MAXDEL] : NAN;
+                H.max_delta = (H.win_n >= P.T) ? s_sl[SL_MAXDEL].hi : NAN;
                 H.acc = NAN;
                 H.nonfinite_last = (int)nbad;
                 H.nonfinite_total += (int)nbad;
-                bool sw = (H.win_n >= P.T) && (s_fin[NCS + SL_MAXDEL] < P.switch_tol);
+                bool sw = (H.win_n >= P.T) && (s_sl[SL_MAXDEL].hi < P.switch_tol);
                 if (P.force_switch_at > 0) sw = H.t >= P.force_switch_at;
                 if (sw && P.adjusted && H.t < P.n_total) {
                     s_switch = 1;
-                    if (sum_var > 0) H.eps *= sqrt(d / sum_var);
+                    if (sum_var > 0.0f) H.eps *= sqrtf(d / sum_var);
                     H.integ = (P.d > P.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
                     H.a_target = (H.integ == INTEG_MN4) ? P.a_target_mn4 : P.a_target_mn2;
                     H.L = P.adj_L_factor * P.N * H.eps;
-                    H.lo = 0.0;
-                    H.hi = 0.0;
+                    H.lo = 0.0f;
+                    H.hi = 0.0f;
                     H.adapting = 1;
                     H.p = 0;
                     H.phase = 1;
@@ -603,17 +673,17 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 }
             } else {
                 // Sec. 5.1: mean acceptance, bisection until |a - a*| <= tol
-                const double a = s_fin[CS_ASUM] / (double)P.M;
-                const double nbad = s_fin[CS_NBAD];
+                const float a = ff_f(s_tot[CS_ASUM]) / (float)P.M;
+                const float nbad = ff_f(s_tot[CS_NBAD]);
                 H.eps_used = H.eps;
-                H.adapting = H.adapting && (fabs(a - H.a_target) > P.acc_tol);
+                H.adapting = H.adapting && (fabsf(a - H.a_target) > P.acc_tol);
                 if (H.adapting) {
                     if (a > H.a_target) {
                         H.lo = H.eps;
-                        H.eps = (H.hi > 0) ? 0.5 * (H.lo + H.hi) : 2.0 * H.eps;
+                        H.eps = (H.hi > 0.0f) ? 0.5f * (H.lo + H.hi) : 2.0f * H.eps;
                     } else {
                         H.hi = H.eps;
-                        H.eps = (H.lo > 0) ? 0.5 * (H.lo + H.hi) : 0.5 * H.eps;
+                        H.eps = (H.lo > 0.0f) ? 0.5f * (H.lo + H.hi) : 0.5f * H.eps;
                     }
                 }
                 H.L = P.adj_L_factor * P.N * H.eps;
@@ -627,18 +697,19 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 if (H.t + P.N > P.n_total) H.done = 1;
             }
             if (P.mode == 1) H.iters += 1;
+            if (s_bad) atomicCAS(P.status, ST_OK, ST_BADPARAM);
             H.sum_var = sum_var;
             const uint64_t now = global_ns();
             if (P.Ex2) {
-                H.b2_avg = s_fin[NCS + SL_B2SUM] / d;
-                H.b2_max = s_fin[NCS + SL_B2MAX];
-                const double b2 = P.stop_b2_max ? H.b2_max : H.b2_avg;
-                if (H.b2_first_t < 0 && b2 < 0.01) {
+                H.b2_avg = ff_f(s_sl[SL_B2SUM]) / d;
+                H.b2_max = s_sl[SL_B2MAX].hi;
+                const float b2 = P.stop_b2_max ? H.b2_max : H.b2_avg;
+                if (H.b2_first_t < 0 && b2 < 0.01f) {
                     H.b2_first_t = H.t;
                     H.b2_first_grads = H.grads;
                     H.b2_first_ns = (double)(now - H.t0_ns);
                 }
-                if (P.stop_b2 > 0 && b2 < P.stop_b2) H.done = 1;
+                if (P.stop_b2 > 0.0f && b2 < P.stop_b2) H.done = 1;
             } else {
                 H.b2_avg = H.b2_max = NAN;
             }
@@ -676,8 +747,8 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                     const int i = 4 * j + c;
                     float s = 1.0f;
                     if (j < P.nblk && i < P.d) {
-                        const double v = __ldcg(&P.var_y[i]);
-                        s = v > 0.0 ? (float)sqrt(v) : 1.0f;
+                        const float v = s_var[i];
+                        s = v > 0.0f ? sqrtf(v) : 1.0f;
                     }
                     const int q = 4 * k + c;
                     sg[q] = s;
@@ -685,14 +756,15 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                     g[q] = g[q] * s;
                 }
             }
-            for (int i = i0 + tid; i < i1; i += blockDim.x) {
-                const double v = __ldcg(&P.var_y[i]);
-                P.sigma[i] = v > 0.0 ? (float)sqrt(v) : 1.0f;
-            }
+            if (blockIdx.x == 0)
+                for (int i = tid; i < P.d; i += blockDim.x) {
+                    const float v = s_var[i];
+                    P.sigma[i] = v > 0.0f ? sqrtf(v) : 1.0f;
+                }
         }
     }
 
-    // ---- store the state and (block 0) the phase machine
+    // ---- store the state and (block 0) the phase machine and window sums
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         const int j = gl + LPC * k;
@@ -703,13 +775,14 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             *reinterpret_cast<float4*>(P.g + off) = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
         }
     }
-    if (active && gl == 0) P.logp[m] = ff_to_double(lp);
-    if (blockIdx.x == 0 && tid == 0) *P.hyper = H;
+    if (active && gl == 0) P.logp_ff[m] = make_float2(lp.hi, lp.lo);
+    if (blockIdx.x == 0) {
+        for (int i = tid; i < dp; i += blockDim.x) {
+            P.win_sums[i] = s_win[i];
+            P.var_y[i] = s_var[i];
+        }
+        if (tid == 0) *P.hyper = H;
+    }
 }
-
-// Host-side dispatch helpers, defined per target in laps_resident_<kind>.cu.
-struct ResidentShape {
-    int lpc, cpl;
-};
 
 }  // namespace laps

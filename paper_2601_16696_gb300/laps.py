@@ -42,7 +42,8 @@ class Config(C.Structure):
                 ("a_target_mn2", C.c_double), ("a_target_mn4", C.c_double),
                 ("n_total_steps", C.c_int), ("steps_per_proposal", C.c_int),
                 ("mn4_min_dim", C.c_int), ("eevpd_centered", C.c_int), ("adjusted", C.c_int),
-                ("force_switch_at", C.c_int), ("stop_b2", C.c_double), ("stop_b2_max", C.c_int),
+                ("force_switch_at", C.c_int), ("fixed_eps", C.c_double),
+                ("stop_b2", C.c_double), ("stop_b2_max", C.c_int),
                 ("precision", C.c_int), ("barrier_timeout_ns", C.c_int64),
                 ("chains_per_block", C.c_int), ("lanes_per_chain", C.c_int),
                 ("coords_per_lane", C.c_int), ("barrier_extra_arrivals", C.c_int)]
