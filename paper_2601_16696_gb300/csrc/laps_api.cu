@@ -225,9 +225,10 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.G = c->G;
     P.qpp = c->qpp;
     P.bar_extra = g.barrier_extra_arrivals;
+    P.phase_ns = c->phase_ns;
 
     CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
-    CK(cudaMemsetAsync(c->acc, 0, (size_t)3 * c->nacc * 4 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c->acc, 0, (size_t)3 * c->nacc * 4 * FX_STRIDE * sizeof(unsigned long long), st));
     const Coefs* cf = c->coefs;
     void* args[] = {&P, &cf};
     CK(cudaLaunchCooperativeKernel(c->fn, dim3(c->G), dim3(c->threads), args, c->smem, st));
@@ -344,7 +345,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
               alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp_ff, M * 8) &&
               alloc((void**)&c->sigma, c->d_pad * 4) &&
-              alloc((void**)&c->acc, (size_t)3 * c->nacc * 4 * 8) &&
+              alloc((void**)&c->acc, (size_t)3 * c->nacc * 4 * FX_STRIDE * 8) &&
               alloc((void**)&c->var_y, c->d_pad * 4) &&
               alloc((void**)&c->ring, (size_t)(c->T + 1) * c->d_pad * 8) &&
               alloc((void**)&c->win_sums, (size_t)c->d_pad * 16) &&
@@ -481,6 +482,8 @@ static laps_status read_status(laps_ctx* c) {
     CK(cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
     if (s == ST_NONFINITE) return fail(LAPS_ERR_NONFINITE, "non-finite initial position, log p or gradient");
+    if (s == ST_OVERFLOW)
+        return fail(LAPS_ERR_NONFINITE, "an ensemble sum left the accumulator range (|sum| >= 2^77): the run diverged");
     if (s != 0) return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
     return LAPS_OK;
 }
@@ -597,6 +600,23 @@ laps_status laps_restore(laps_ctx* c, const void* blob, size_t size) {
     CK(cudaMemset(c->status, 0, sizeof(int)));
     return LAPS_OK;
 }
+
+#ifdef LAPS_PHASE_TIMING
+// diagnostic build only (not part of the ABI): per-phase device time of block 0
+laps_status laps_debug_phase_ns(laps_ctx* c, unsigned long long* out) {
+    if (!c->phase_ns) {
+        CK(cudaMalloc(&c->phase_ns, 8 * sizeof(unsigned long long)));
+        c->allocs.push_back(c->phase_ns);
+        CK(cudaMemset(c->phase_ns, 0, 8 * sizeof(unsigned long long)));
+    }
+    if (out) {
+        CK(cudaStreamSynchronize(c->last_stream));
+        CK(cudaMemcpy(out, c->phase_ns, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(c->phase_ns, 0, 8 * sizeof(unsigned long long)));
+    }
+    return LAPS_OK;
+}
+#endif
 
 laps_status laps_get_launch_info(const laps_ctx* c, laps_launch_info* o) {
     if (!c || !o) return fail(LAPS_ERR_INVALID_ARG, "null argument");

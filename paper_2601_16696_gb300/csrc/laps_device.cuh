@@ -11,7 +11,7 @@
 namespace laps {
 
 // ---------------------------------------------------------------- status codes
-enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5 };
+enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5, ST_OVERFLOW = 6 };
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Ten rounds; each multiplies words 0 and 2 by the round multipliers, xors the
@@ -118,11 +118,13 @@ __device__ __forceinline__ double warp_max_d(double v) {
 
 // ---------------------------------------------------------------- fixed point
 // Exact, order-independent accumulation across blocks: a value is converted to
-// a 128-bit two's-complement integer with 64 fractional bits (|v| < 2^62,
-// resolution 2^-64), split into four 32-bit limbs, and each limb is added with
-// a 64-bit integer atomic into its own accumulator.  Integer addition commutes,
-// so the totals, and everything computed from them, are bit-identical from run
-// to run whatever order the blocks arrive in.
+// a 128-bit two's-complement integer with FX_FRAC = 48 fractional bits
+// (resolution 2^-48 ~ 3.6e-15, range |v| < 2^77 ~ 1.5e23), split into four
+// 32-bit limbs, and each limb is added with a 64-bit integer atomic into its
+// own accumulator.  Integer addition commutes, so the totals, and everything
+// computed from them, are bit-identical from run to run whatever order the
+// blocks arrive in.  A value outside the range (or not finite) raises `bad`.
+constexpr int FX_FRAC = 48;
 struct i128 {
     unsigned long long lo;
     long long hi;
@@ -134,7 +136,7 @@ __device__ __forceinline__ i128 f32_to_fx(float f, int& bad) {
     if (e == 0) return r;  // zero or subnormal: below the resolution
     if (e == 0xff) { bad = 1; return r; }
     const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // |f| = m 2^(e-150)
-    const int sh = e - 150 + 64;  // bit position of m's lsb in |f| 2^64
+    const int sh = e - 150 + FX_FRAC;  // bit position of m's lsb in |f| 2^FX_FRAC
     if (sh < 0) {
         if (sh > -24) r.lo = m >> (-sh);
     } else if (sh < 64) {
@@ -158,29 +160,34 @@ __device__ __forceinline__ i128 fx_add(i128 a, i128 b) {
     r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ll : 0ll);
     return r;
 }
-// acc: four u64 limb accumulators of one quantity
+// Each limb accumulator sits alone in a 128-byte line (FX_STRIDE u64 apart):
+// integer atomics to one L2 line serialise, so limbs sharing lines would make
+// every block's additions queue behind each other.
+constexpr int FX_STRIDE = 16;
+// acc: the four limb accumulators of one quantity, FX_STRIDE apart
 __device__ __forceinline__ void fx_atomic_add(unsigned long long* acc, ff v, int& bad) {
     const i128 x = fx_add(f32_to_fx(v.hi, bad), f32_to_fx(v.lo, bad));
-    atomicAdd(acc + 0, x.lo & 0xffffffffull);
-    atomicAdd(acc + 1, x.lo >> 32);
-    atomicAdd(acc + 2, (unsigned long long)x.hi & 0xffffffffull);
-    atomicAdd(acc + 3, (unsigned long long)(x.hi >> 32));  // arithmetic shift: signed limb
+    atomicAdd(acc + 0 * FX_STRIDE, x.lo & 0xffffffffull);
+    atomicAdd(acc + 1 * FX_STRIDE, x.lo >> 32);
+    atomicAdd(acc + 2 * FX_STRIDE, (unsigned long long)x.hi & 0xffffffffull);
+    atomicAdd(acc + 3 * FX_STRIDE, (unsigned long long)(x.hi >> 32));  // signed limb
 }
-// total of the four limb sums as a float-float (no FP64 arithmetic)
+// total of the four limb sums: exact 128-bit integer, then to FP64 (53 bits)
+// and split into a float-float
 __device__ __forceinline__ ff fx_read(const unsigned long long* acc) {
-    const unsigned long long a0 = __ldcg(acc + 0), a1 = __ldcg(acc + 1), a2 = __ldcg(acc + 2);
-    const long long a3 = (long long)__ldcg(acc + 3);
+    const unsigned long long a0 = __ldcg(acc + 0 * FX_STRIDE), a1 = __ldcg(acc + 1 * FX_STRIDE);
+    const unsigned long long a2 = __ldcg(acc + 2 * FX_STRIDE);
+    const long long a3 = (long long)__ldcg(acc + 3 * FX_STRIDE);
     const unsigned long long t0 = a0;
     const unsigned long long t1 = a1 + (t0 >> 32);
     const unsigned long long t2 = a2 + (t1 >> 32);
     const long long t3 = a3 + (long long)(t2 >> 32);
     const unsigned long long lo = (t0 & 0xffffffffull) | (t1 << 32);
     const long long hi = (long long)((t2 & 0xffffffffull) | ((unsigned long long)t3 << 32));
-    const float fh = __ll2float_rn(hi);                 // integer part, rounded
-    const long long rest = hi - __float2ll_rn(fh);      // exact remainder of the integer part
-    const float fl = __ll2float_rn(rest) + __ull2float_rn(lo) * 5.421010862427522e-20f;  // 2^-64
-    const float s = fh + fl;
-    return ff{s, fl - (s - fh)};
+    // value = (hi 2^64 + lo) 2^-48 = hi 2^16 + lo 2^-48
+    const double v = fma((double)hi, 65536.0, (double)lo * 3.552713678800501e-15);
+    const float h = (float)v;
+    return ff{h, (float)(v - (double)h)};
 }
 
 // ---------------------------------------------------------------- timers, barrier

@@ -30,6 +30,7 @@ struct laps_ctx {
     float2* Ex2 = nullptr;
     float* inv_varx2 = nullptr;
     int qpp = 1;
+    unsigned long long* phase_ns = nullptr;  // diagnostic build: per-phase time (not owned)
     laps::Hyper* hyper = nullptr;
     laps_trace_row* trace = nullptr;
     unsigned* bar = nullptr;

@@ -68,6 +68,7 @@ struct KParams {
     int G;          // blocks in the grid
     int qpp;        // per-coordinate quantities reduced per shared-memory pass
     int bar_extra;  // extra arrivals every barrier waits for (test hook; 0 normally)
+    unsigned long long* phase_ns;  // diagnostic build only: [5] time per phase
 };
 
 }  // namespace laps

@@ -271,31 +271,24 @@ __device__ __forceinline__ ff ff_divf(ff a, float b) {
 }
 __device__ __forceinline__ float ff_f(ff a) { return a.hi + a.lo; }
 
-// block-wide reductions in a fixed order (identical in every block)
-__device__ __forceinline__ ff block_sum_ff(ff v, ff* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = group_sum_ff<32>(v);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    ff s = ff_make(0.0f);
-    for (int w = 0; w < nw; ++w) s = ff_add(s, sh[w]);
-    return s;
-}
-__device__ __forceinline__ float block_max(float v, float* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = (w > v || w != w) ? w : v;
-    }
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    float s = 0.0f;
-    for (int w = 0; w < nw; ++w) s = (sh[w] > s || sh[w] != sh[w]) ? sh[w] : s;
-    return s;
-}
+// ---------------------------------------------------------------- phase timing
+// Built only with -DLAPS_PHASE_TIMING (a diagnostic build): block 0 adds the
+// %globaltimer time spent between consecutive marks to P.phase_ns[k].
+#ifdef LAPS_PHASE_TIMING
+#define LAPS_PHASE_MARK(k)                                                              \
+    do {                                                                                \
+        __syncthreads();                                                                \
+        if (blockIdx.x == 0 && threadIdx.x == 0 && P.phase_ns) {                        \
+            const unsigned long long now_ = global_ns();                                \
+            if ((k) > 0) P.phase_ns[(k) - 1] += now_ - phase_t_;                        \
+            phase_t_ = now_;                                                            \
+        }                                                                               \
+    } while (0)
+#else
+#define LAPS_PHASE_MARK(k) \
+    do {                   \
+    } while (0)
+#endif
 
 // ---------------------------------------------------------------- the kernel
 template <int KIND, int LPC, int CPL>
@@ -306,12 +299,13 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Hyper H;
     __shared__ Coefs CF;
-    __shared__ ff s_red[kMaxThreads / 32];
-    __shared__ float s_redf[kMaxThreads / 32];
+    __shared__ ff s_wsum[3][kMaxThreads / 32];    // per-warp sums: Var, (1 - V)^2, b^2
+    __shared__ float s_wmax[2][kMaxThreads / 32];  // per-warp maxima: delta, b^2
     __shared__ ff s_tot[NCS];
     __shared__ ff s_sl[NSL];
     __shared__ int s_switch, s_bad;
     __shared__ float s_eps, s_c1, s_c2s;  // step scalars of the next iteration
+    __shared__ unsigned long long s_now;  // %globaltimer at the last finalise
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -322,7 +316,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     const bool active = m < P.M;
     const int dp = P.d_pad;
     const unsigned gmask = ((LPC == 32) ? 0xffffffffu : ((1u << LPC) - 1u)) << (grp * LPC);
-    const size_t acc_set = (size_t)P.nacc * 4;  // u64 limbs per accumulator set
+    const size_t acc_set = (size_t)P.nacc * 4 * FX_STRIDE;  // u64 words per accumulator set
 
     // dynamic shared memory: per-warp column sums, per-chain scalars,
     // per-coordinate variance (for the switch), window sums
@@ -412,8 +406,12 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     }
 
     const int n_iter = (P.mode == 0) ? 1 : P.n_iters;
+#ifdef LAPS_PHASE_TIMING
+    unsigned long long phase_t_ = 0;
+#endif
     for (int it = 0; it < n_iter; ++it) {
         if (P.mode == 1 && H.done) break;
+        LAPS_PHASE_MARK(0);
         // ------------------------------------------------ 1. chain update
         ff c_d = ff_make(0.0f);
         float c_d2 = 0.0f, c_fin = 0.0f, c_bad = 0.0f, c_a = 0.0f;
@@ -490,6 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 }
             }
         }
+        LAPS_PHASE_MARK(1);
         // ------------------------------------------------ 2. block sums -> fixed-point totals
         unsigned long long* acc = P.acc + (size_t)(it % 3) * acc_set;
         {   // clear this block's share of the set the next iteration adds into
@@ -523,7 +522,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 ff s = ff_make(0.0f);
                 const float* src = sq + (size_t)(qd - q0) * nwarps * dp + i;
                 for (int w = 0; w < nwarps; ++w) s = ff_add(s, src[(size_t)w * dp]);
-                fx_atomic_add(acc + ((size_t)qd * dp + i) * 4, s, fx_bad);
+                fx_atomic_add(acc + ((size_t)qd * dp + i) * (4 * FX_STRIDE), s, fx_bad);
             }
             __syncthreads();
         }
@@ -539,13 +538,15 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 if (tid == CS_DSUM) s = ff_add(s, ff{cs[0], cs[1]});
                 else s = ff_add(s, cs[tid + 1]);
             }
-            fx_atomic_add(acc + ((size_t)NQ * dp + tid) * 4, s, fx_bad);
+            fx_atomic_add(acc + ((size_t)NQ * dp + tid) * (4 * FX_STRIDE), s, fx_bad);
         }
         if (fx_bad) atomicOr(&s_bad, 1);
+        LAPS_PHASE_MARK(2);
         // ------------------------------------------------ 3. the one grid barrier
         if (!grid_sync_count(P.bar_count, P.status, (unsigned)(it + 1) * (unsigned)(G + P.bar_extra),
                              P.timeout_ns))
             return;
+        LAPS_PHASE_MARK(3);
         // ------------------------------------------------ 4. statistics (every block)
         const bool push = (P.mode == 1 && H.phase == 0);
         const bool have_g = nq == NQ;
@@ -555,8 +556,8 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         ff a_var = ff_make(0.0f), a_dv = ff_make(0.0f), a_b2 = ff_make(0.0f);
         float a_del = 0.0f, a_b2m = 0.0f;
         for (int i = tid; i < P.d; i += blockDim.x) {
-            const ff sy = fx_read(acc + ((size_t)0 * dp + i) * 4);
-            const ff syy = fx_read(acc + ((size_t)1 * dp + i) * 4);
+            const ff sy = fx_read(acc + ((size_t)0 * dp + i) * (4 * FX_STRIDE));
+            const ff syy = fx_read(acc + ((size_t)1 * dp + i) * (4 * FX_STRIDE));
             const ff mean = ff_mulf(sy, iM), ey2 = ff_mulf(syy, iM);
             const float var_y = ff_f(ff_add(ey2, ff_neg(ff_mul(mean, mean))));
             const float sgi = P.sigma[i];
@@ -565,8 +566,8 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             a_var = ff_add(a_var, s2i * var_y);
             s_var[i] = var_y;
             if (have_g) {
-                const ff sg_ = fx_read(acc + ((size_t)2 * dp + i) * 4);
-                const ff syg = fx_read(acc + ((size_t)3 * dp + i) * 4);
+                const ff sg_ = fx_read(acc + ((size_t)2 * dp + i) * (4 * FX_STRIDE));
+                const ff syg = fx_read(acc + ((size_t)3 * dp + i) * (4 * FX_STRIDE));
                 // V_ii = -(E[y g] - E[y] E[g])  (App. B, Eq. ECA)
                 const float V = -ff_f(ff_add(ff_mulf(syg, iM), ff_neg(ff_mul(mean, ff_mulf(sg_, iM)))));
                 a_dv = ff_add(a_dv, (1.0f - V) * (1.0f - V));
@@ -601,19 +602,44 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 a_b2m = (b2 > a_b2m || b2 != b2) ? b2 : a_b2m;
             }
         }
-        {
-            const ff v0 = block_sum_ff(a_var, s_red);
-            const ff v1 = block_sum_ff(a_dv, s_red);
-            const ff v3 = block_sum_ff(a_b2, s_red);
-            const float v2 = block_max(a_del, s_redf);
-            const float v4 = block_max(a_b2m, s_redf);
-            if (tid == 0) {
-                s_sl[SL_VAR] = v0; s_sl[SL_DV] = v1; s_sl[SL_B2SUM] = v3;
-                s_sl[SL_MAXDEL] = ff_make(v2); s_sl[SL_B2MAX] = ff_make(v4);
+        {   // one fused block reduction in a fixed order: warp butterflies, then warps in order
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const ff w0{__shfl_xor_sync(0xffffffffu, a_var.hi, o), __shfl_xor_sync(0xffffffffu, a_var.lo, o)};
+                const ff w1{__shfl_xor_sync(0xffffffffu, a_dv.hi, o), __shfl_xor_sync(0xffffffffu, a_dv.lo, o)};
+                const ff w3{__shfl_xor_sync(0xffffffffu, a_b2.hi, o), __shfl_xor_sync(0xffffffffu, a_b2.lo, o)};
+                const float w2 = __shfl_xor_sync(0xffffffffu, a_del, o);
+                const float w4 = __shfl_xor_sync(0xffffffffu, a_b2m, o);
+                a_var = ff_add(a_var, w0);
+                a_dv = ff_add(a_dv, w1);
+                a_b2 = ff_add(a_b2, w3);
+                a_del = (w2 > a_del || w2 != w2) ? w2 : a_del;
+                a_b2m = (w4 > a_b2m || w4 != w4) ? w4 : a_b2m;
+            }
+            if (lane == 0) {
+                s_wsum[0][warp] = a_var;
+                s_wsum[1][warp] = a_dv;
+                s_wsum[2][warp] = a_b2;
+                s_wmax[0][warp] = a_del;
+                s_wmax[1][warp] = a_b2m;
             }
         }
-        if (tid < NCS) s_tot[tid] = fx_read(acc + ((size_t)NQ * dp + tid) * 4);
+        if (tid < NCS) s_tot[tid] = fx_read(acc + ((size_t)NQ * dp + tid) * (4 * FX_STRIDE));
         __syncthreads();
+        if (tid == 0) {
+            ff v0 = ff_make(0.0f), v1 = v0, v3 = v0;
+            float v2 = 0.0f, v4 = 0.0f;
+            for (int w = 0; w < nwarps; ++w) {
+                v0 = ff_add(v0, s_wsum[0][w]);
+                v1 = ff_add(v1, s_wsum[1][w]);
+                v3 = ff_add(v3, s_wsum[2][w]);
+                v2 = (s_wmax[0][w] > v2 || s_wmax[0][w] != s_wmax[0][w]) ? s_wmax[0][w] : v2;
+                v4 = (s_wmax[1][w] > v4 || s_wmax[1][w] != s_wmax[1][w]) ? s_wmax[1][w] : v4;
+            }
+            s_sl[SL_VAR] = v0; s_sl[SL_DV] = v1; s_sl[SL_B2SUM] = v3;
+            s_sl[SL_MAXDEL] = ff_make(v2); s_sl[SL_B2MAX] = ff_make(v4);
+        }
+        LAPS_PHASE_MARK(4);
         // ------------------------------------------------ 5. finalise (identical in every block)
         if (tid == 0) {
             const float d = (float)P.d;
@@ -697,7 +723,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 if (H.t + P.N > P.n_total) H.done = 1;
             }
             if (P.mode == 1) H.iters += 1;
-            if (s_bad) atomicCAS(P.status, ST_OK, ST_BADPARAM);
+            if (s_bad) atomicCAS(P.status, ST_OK, ST_OVERFLOW);
             H.sum_var = sum_var;
             const uint64_t now = global_ns();
             if (P.Ex2) {
@@ -714,29 +740,32 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 H.b2_avg = H.b2_max = NAN;
             }
             set_step_scalars(H, P.d, s_eps, s_c1, s_c2s);
-            if (blockIdx.x == 0 && H.iters < P.trace_cap) {
-                laps_trace_row r;
-                r.phase = H.phase;
-                r.t = H.t;
-                r.eps = H.eps;
-                r.L = H.L;
-                r.eps_used = P.mode == 0 ? NAN : H.eps_used;
-                r.eevpd = P.mode == 0 ? NAN : H.eevpd;
-                r.eevpd_wanted = P.mode == 0 ? NAN : H.eevpd_wanted;
-                r.dtilde = P.mode == 0 ? NAN : H.dtilde;
-                r.max_delta = P.mode == 0 ? NAN : H.max_delta;
-                r.acc = P.mode == 0 ? NAN : H.acc;
-                r.b2_max = H.b2_max;
-                r.b2_avg = H.b2_avg;
-                r.sum_var = sum_var;
-                r.nonfinite = P.mode == 0 ? 0 : H.nonfinite_last;
-                r.adapting = H.adapting;
-                r.grads = H.grads;
-                r.time_ns = (double)(now - H.t0_ns);
-                P.trace[H.iters] = r;
-            }
+            s_now = now;
         }
         __syncthreads();
+        // the trace row (block 0), written by the last warp while the others go on
+        if (blockIdx.x == 0 && tid == blockDim.x - 32 && H.iters < P.trace_cap) {
+            laps_trace_row r;
+            r.phase = H.phase;
+            r.t = H.t;
+            r.eps = H.eps;
+            r.L = H.L;
+            r.eps_used = P.mode == 0 ? NAN : H.eps_used;
+            r.eevpd = P.mode == 0 ? NAN : H.eevpd;
+            r.eevpd_wanted = P.mode == 0 ? NAN : H.eevpd_wanted;
+            r.dtilde = P.mode == 0 ? NAN : H.dtilde;
+            r.max_delta = P.mode == 0 ? NAN : H.max_delta;
+            r.acc = P.mode == 0 ? NAN : H.acc;
+            r.b2_max = H.b2_max;
+            r.b2_avg = H.b2_avg;
+            r.sum_var = H.sum_var;
+            r.nonfinite = P.mode == 0 ? 0 : H.nonfinite_last;
+            r.adapting = H.adapting;
+            r.grads = H.grads;
+            r.time_ns = (double)(s_now - H.t0_ns);
+            P.trace[H.iters] = r;
+        }
+        LAPS_PHASE_MARK(5);
         if (s_switch) {
             // Sec. 4: diagonal preconditioner y = x / Var[x]^{1/2}, fixed from now on
 #pragma unroll

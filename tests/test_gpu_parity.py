@@ -162,13 +162,14 @@ def test_first_ten_steps_adaptive(L, ora, name):
 
 
 # ------------------------------------------------------------------ whole runs
-def _final_b2(trace, key, frac=0.25):
-    """b^2 of the final ensembles: the mean over the last quarter of the
+def _final_b2(trace, key, frac=0.5):
+    """b^2 of the final ensembles: the mean over the last half of the
     iterations of the final phase.  One ensemble's b^2 is dominated by its
     finite-M noise (a chi^2-like draw: ~14% spread for b^2_avg at d = 100,
     ~50% for b^2_max), and the GPU and oracle runs decorrelate after a few
     tens of steps, so single final values differ by that noise; the tail mean
-    averages many decorrelated ensembles (seed-to-seed spread 1-5%)."""
+    averages many decorrelated ensembles (oracle seed-to-seed spread 1-5% for
+    b^2_avg, ~10% for b^2_max)."""
     rows = [r for r in trace[1:] if r["phase"] == trace[-1]["phase"]]
     n = max(1, int(len(rows) * frac))
     return float(np.mean([r[key] for r in rows[-n:]]))
@@ -295,15 +296,16 @@ def test_nonfinite_start_is_reported(L):
 
 
 def test_nonfinite_step_is_reverted(L, ora):
-    """A step that overflows leaves every chain where it was and halves eps."""
+    """A step that overflows (binary32 on the GPU, cosh in the oracle) leaves
+    every chain where it was and halves eps."""
     pr = W.gauss_diag(d=10, M=64, n_steps=20)
-    s = _gpu(L, pr, seed=0, eps0_coef=1e9)
+    s = _gpu(L, pr, seed=0, eps0_coef=1e30)
     x0 = s.sample().cpu().numpy()
     s.step(1)
     st = s.stats()
     assert st["nonfinite_total"] == 64
     np.testing.assert_array_equal(s.sample().cpu().numpy(), x0)
-    r = _ora(ora, pr, seed=0, eps0_coef=1e9)
+    r = _ora(ora, pr, seed=0, eps0_coef=1e30)
     r.iterate(1)
     assert st["eps"] == pytest.approx(r.trace[1]["eps"], rel=1e-6)
 
