@@ -219,6 +219,29 @@ laps_status laps_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64
 laps_status laps_normals(uint64_t seed, uint32_t m0, int64_t nm, uint32_t t, uint32_t tag,
                          uint32_t pid, int64_t d, float* out, void* stream);
 
+/* ---- a run that allocates nothing ---------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a process whose device memory belongs to a pool
+ * allocator that reserved the GPU at start-up, code that must not add the
+ * device-wide synchronisation cudaMalloc/cudaFree imply, a plug-in that may
+ * not grow the device footprint after loading).
+ * One complete run (laps_init with x0 / x0_scale / seed, then laps_run) of a
+ * GAUSS_DIAG, BANANA or FUNNEL target described by desc (its device arrays
+ * are read, not copied into any allocation); the samples go to x_out device
+ * [M][d]; if stats_out is not NULL the call synchronises the stream and fills
+ * it.  No trace is kept and laps_set_truth does not apply (b^2 fields NaN).
+ * All scratch lives in one fixed 16 MiB __device__ array of the library that
+ * every GPU loading the library holds until exit; a problem needing more
+ * (about 12 M d bytes of state plus the window and reduction buffers) returns
+ * LAPS_ERR_INVALID_ARG before any launch.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * clears what must start at zero; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised. */
+laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M, const laps_config* cfg,
+                             const float* x0, double x0_scale, uint64_t seed, float* x_out,
+                             laps_stats* stats_out, void* stream);
+
 /* Launch shape the context uses (for tests and the autotuner). */
 typedef struct {
     int chains_per_block, lanes_per_chain, coords_per_lane, threads, blocks;

@@ -78,7 +78,15 @@ __global__ void fill_kernel(float* p, float v, int64_t n) {
 
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
-static void coefs_table(Coefs& cf) {
+void launch_fill(float* p, float v, int64_t n, cudaStream_t st) {
+    fill_kernel<<<grid_for(n), 256, 0, st>>>(p, v, n);
+}
+void launch_unpack(const float* src, const float* scale, float* dst, int64_t M, int d, int d_pad,
+                   cudaStream_t st) {
+    unpack_rows_kernel<<<grid_for(M * d), 256, 0, st>>>(src, scale, dst, M, d, d_pad);
+}
+
+void coefs_table(Coefs& cf) {
     std::memset(&cf, 0, sizeof(cf));
     // LF: B_{eps/2} A_eps B_{eps/2}
     cf.K[INTEG_LF] = 2;
@@ -122,7 +130,8 @@ laps_status choose_shape(laps_ctx* c) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int kind = c->tg->kind;
     struct Cand { int lpc, cpl, threads, G; size_t smem; double score; };
-    std::vector<Cand> ok;
+    Cand ok[3 * sizeof(kShapes) / sizeof(kShapes[0])];  // fixed storage: no heap use
+    int n_ok = 0;
     for (auto& sh : kShapes) {
         const int lpc = sh[0], cpl = sh[1];
         if (lpc * cpl < c->d_pad) continue;
@@ -146,15 +155,16 @@ laps_status choose_shape(laps_ctx* c) {
             // fewest blocks (one barrier arrival and one set of atomics per block),
             // then the smallest per-lane footprint
             const double score = (double)G * 100.0 + cpl;
-            ok.push_back({lpc, cpl, threads, G, smem, score});
+            if (n_ok < (int)(sizeof(ok) / sizeof(ok[0]))) ok[n_ok++] = {lpc, cpl, threads, G, smem, score};
         }
     }
-    if (ok.empty())
+    if (n_ok == 0)
         return fail(LAPS_ERR_UNSUPPORTED,
                     "no register-resident launch shape holds M=" + std::to_string(c->M) +
                         " chains of d=" + std::to_string(c->d) + " co-resident on this GPU");
-    auto best = *std::min_element(ok.begin(), ok.end(),
-                                  [](const Cand& a, const Cand& b) { return a.score < b.score; });
+    Cand best = ok[0];
+    for (int k = 1; k < n_ok; ++k)
+        if (ok[k].score < best.score) best = ok[k];
     c->lpc = best.lpc;
     c->cpl = best.cpl;
     c->threads = best.threads;
@@ -393,11 +403,11 @@ laps_status laps_set_truth(laps_ctx* c, const double* Ex2, const double* Varx2) 
     return LAPS_OK;
 }
 
-laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t seed, void* stream) {
-    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
-    if (x0 && !aligned(x0, 4)) return fail(LAPS_ERR_INVALID_ARG, "x0 must be 4-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    c->seed = seed;
+}  // extern "C"
+
+namespace laps {
+// the phase machine before Alg. 1's first line
+static Hyper initial_hyper() {
     Hyper h;
     std::memset(&h, 0, sizeof(h));
     h.phase = 0;
@@ -410,6 +420,13 @@ laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t se
     h.b2_first_ns = NAN;
     h.eevpd = h.eevpd_wanted = h.dtilde = h.max_delta = h.acc = NAN;
     h.b2_max = h.b2_avg = NAN;
+    return h;
+}
+
+// clears the run state (phase machine, status, window, preconditioner) and
+// launches the initialisation; no allocation
+laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st) {
+    const Hyper h = initial_hyper();
     CK(cudaMemcpyAsync(c->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->ring, 0, (size_t)(c->T + 1) * c->d_pad * 8, st));
@@ -420,7 +437,52 @@ laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t se
     // keep the caller's stream synchronous with the host copy of h above
     CK(cudaStreamSynchronize(st));
     c->initialized = true;
-    return launch_resident(c, 0, 1, x0, (float)x0_scale, st);
+    return launch_resident(c, 0, 1, x0, x0_scale, st);
+}
+
+laps_status status_error(int s) {
+    if (s == ST_OK) return LAPS_OK;
+    if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
+    if (s == ST_NONFINITE) return fail(LAPS_ERR_NONFINITE, "non-finite initial position, log p or gradient");
+    if (s == ST_OVERFLOW)
+        return fail(LAPS_ERR_NONFINITE, "an ensemble sum left the accumulator range (|sum| >= 2^77): the run diverged");
+    return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
+}
+
+void stats_from_hyper(const Hyper& h, laps_stats* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->phase = h.phase;
+    o->t = h.t;
+    o->t_switch = h.t_switch;
+    o->integrator = h.integ;
+    o->adapting = h.adapting;
+    o->done = h.done;
+    o->iterations = h.iters;
+    o->nonfinite_total = h.nonfinite_total;
+    o->grads = h.grads;
+    o->eps = h.eps;
+    o->L = h.L;
+    o->eevpd = h.eevpd;
+    o->eevpd_wanted = h.eevpd_wanted;
+    o->dtilde = h.dtilde;
+    o->max_delta = h.max_delta;
+    o->acc = h.acc;
+    o->b2_max = h.b2_max;
+    o->b2_avg = h.b2_avg;
+    o->sum_var = h.sum_var;
+    o->b2_first_t = h.b2_first_t;
+    o->b2_first_grads = h.b2_first_grads;
+    o->b2_first_ns = h.b2_first_ns;
+}
+}  // namespace laps
+
+extern "C" {
+
+laps_status laps_init(laps_ctx* c, const float* x0, double x0_scale, uint64_t seed, void* stream) {
+    if (!c) return fail(LAPS_ERR_INVALID_ARG, "null ctx");
+    if (x0 && !aligned(x0, 4)) return fail(LAPS_ERR_INVALID_ARG, "x0 must be 4-byte aligned");
+    c->seed = seed;
+    return start_run(c, x0, (float)x0_scale, (cudaStream_t)stream);
 }
 
 laps_status laps_step(laps_ctx* c, int n_iters, void* stream) {
@@ -480,12 +542,7 @@ static laps_status read_status(laps_ctx* c) {
     CK(cudaStreamSynchronize(c->last_stream));
     int s = 0;
     CK(cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
-    if (s == ST_NONFINITE) return fail(LAPS_ERR_NONFINITE, "non-finite initial position, log p or gradient");
-    if (s == ST_OVERFLOW)
-        return fail(LAPS_ERR_NONFINITE, "an ensemble sum left the accumulator range (|sum| >= 2^77): the run diverged");
-    if (s != 0) return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
-    return LAPS_OK;
+    return status_error(s);
 }
 
 laps_status laps_get_stats(laps_ctx* c, laps_stats* o) {
@@ -493,29 +550,7 @@ laps_status laps_get_stats(laps_ctx* c, laps_stats* o) {
     laps_status st = read_status(c);
     Hyper h;
     CK(cudaMemcpy(&h, c->hyper, sizeof(h), cudaMemcpyDeviceToHost));
-    std::memset(o, 0, sizeof(*o));
-    o->phase = h.phase;
-    o->t = h.t;
-    o->t_switch = h.t_switch;
-    o->integrator = h.integ;
-    o->adapting = h.adapting;
-    o->done = h.done;
-    o->iterations = h.iters;
-    o->nonfinite_total = h.nonfinite_total;
-    o->grads = h.grads;
-    o->eps = h.eps;
-    o->L = h.L;
-    o->eevpd = h.eevpd;
-    o->eevpd_wanted = h.eevpd_wanted;
-    o->dtilde = h.dtilde;
-    o->max_delta = h.max_delta;
-    o->acc = h.acc;
-    o->b2_max = h.b2_max;
-    o->b2_avg = h.b2_avg;
-    o->sum_var = h.sum_var;
-    o->b2_first_t = h.b2_first_t;
-    o->b2_first_grads = h.b2_first_grads;
-    o->b2_first_ns = h.b2_first_ns;
+    stats_from_hyper(h, o);
     return st;
 }
 

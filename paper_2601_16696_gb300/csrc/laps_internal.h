@@ -49,4 +49,15 @@ struct laps_ctx {
 namespace laps {
 laps_status fail(laps_status st, const std::string& msg);
 laps_status cuda_fail(cudaError_t e, const char* what);
+// shared by the context API and the allocation-free entry point (laps_api.cu)
+laps_status choose_shape(laps_ctx* c);
+laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st);
+laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
+                            cudaStream_t st);
+laps_status status_error(int device_status);
+void stats_from_hyper(const Hyper& h, laps_stats* out);
+void coefs_table(Coefs& cf);
+void launch_fill(float* p, float v, int64_t n, cudaStream_t st);
+void launch_unpack(const float* src, const float* scale, float* dst, int64_t M, int d, int d_pad,
+                   cudaStream_t st);
 }  // namespace laps

@@ -108,6 +108,8 @@ SIGNATURES = {
     "laps_normals": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_uint32, C.c_uint32,
                                C.c_uint32, C.c_int64, _vp, _vp]),
     "laps_get_launch_info": (C.c_int, [_vp, C.POINTER(LaunchInfo)]),
+    "laps_run_noalloc": (C.c_int, [C.POINTER(TargetDesc), C.c_int64, C.POINTER(Config), _vp,
+                                   C.c_double, C.c_uint64, _vp, C.POINTER(Stats), _vp]),
 }
 
 
@@ -308,3 +310,18 @@ def normals(seed: int, m0: int, nm: int, t: int, tag: int, pid: int, d: int,
     _check(lib().laps_normals(seed, m0, nm, t & 0xFFFFFFFF, tag, pid, d, _ptr(out),
                               _stream(stream)))
     return out
+
+
+def run_noalloc(kind: int, d: int, M: int, x0: torch.Tensor | None, seed: int,
+                out: torch.Tensor, prec: torch.Tensor | None = None, banana_sb: float = 0.1,
+                funnel_sv: float = 3.0, x0_scale: float = 1.0, config: Config | None = None,
+                stream=None, **cfg_kw) -> dict:
+    """One whole LAPS run through laps_run_noalloc (no device allocation in the
+    library); samples are written to ``out`` [M, d].  Returns the final stats."""
+    cfg = config if config is not None else default_config(**cfg_kw)
+    desc = TargetDesc(kind, d, prec.data_ptr() if prec is not None else None, banana_sb,
+                      funnel_sv, 0, None, None, 1.0)
+    s = Stats()
+    _check(lib().laps_run_noalloc(C.byref(desc), M, C.byref(cfg), _ptr(x0), x0_scale, seed,
+                                  _ptr(out), C.byref(s), _stream(stream)))
+    return _as_dict(s)
