@@ -41,8 +41,8 @@ UNIT = "chain-grad-evals/s"
 WORKLOAD = dict(name="banana_d100", d=100, M=4096, n_steps=5000, switch_at=1000)
 # algorithmic ALU operations per coordinate and gradient evaluation (the design doc
 # "Roofline of the resident kernel"): LF unadjusted step and MN2 adjusted step
-ALU_OPS_LF = 96.0
-ALU_OPS_MN2_PER_GRAD = 70.0
+ALU_OPS_LF = 117.0
+ALU_OPS_MN2_PER_GRAD = 61.0
 
 
 def _rank_env():
@@ -97,6 +97,30 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def _kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2601_16696_gb300", "csrc")
+    for f in ("laps_resident_kernel.cuh", "laps_resident.cuh", "laps_device.cuh", "laps_params.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the ncu capture in profiles/, or None when the
+    kernel sources changed after that capture."""
+    path = os.path.join(ROOT, "profiles", "resident_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = _kernel_source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == cur:
+            return float(f[2])
+    return None
+
+
 def _cpu_baseline(pr, seconds_hint=True):
     """The oracle, as it stands, on the host cores: the first 500 unadjusted
     iterations of the same ensemble (all M chains)."""
@@ -140,16 +164,36 @@ def run_reference(args):
     return 0
 
 
+def ncu_case():
+    import torch
+    from paper_2601_16696_gb300 import build, laps, workloads
+    build.build()
+    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
+    tg = laps.Target.from_problem(pr)
+    s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, force_switch_at=WORKLOAD["switch_at"])
+    s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)  # resident launch 1
+    s.step(20)                                                                # resident launch 2
+    s.step(200)                                                               # resident launch 3
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": pr.name, "t": s.stats()["t"], "launch": s.launch_info()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="laps", choices=["laps", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="no timing: the workload's launch shape, one launch of 200 unadjusted "
+                         "iterations after two others (the case profiled under ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return ncu_case()
 
     import torch
     rank, world, local = _rank_env()
@@ -245,10 +289,8 @@ def main():
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = nsm * 128 * mhz * 1e6 / 1e9  # FP32-pipe lane issue rate, Gop/s
     achieved = ops / (kms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "resident_banana_d100_traffic.json")
-    if os.path.exists(prof):
-        traffic = json.load(open(prof)).get("bytes_per_launch")
+    traffic = _recorded_traffic("laps_resident_kernel<banana,%d,%d>"
+                                % (info["lanes_per_chain"], info["coords_per_lane"]))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "laps_resident_kernel<banana,%d,%d>" % (info["lanes_per_chain"],

@@ -116,11 +116,13 @@ static int resident_qpp(int d_pad, int threads) {
     int q = (int)std::min<size_t>(NQ, (64 * 1024) / std::max<size_t>(per_q, 1));
     return std::max(1, q);
 }
-static size_t resident_smem(int d_pad, int threads, int lpc) {
+// largest slice of coordinates a block owns in the reduction
+static int resident_smax(int d, int G) { return (d + G - 1) / G; }
+static size_t resident_smem(int d_pad, int threads, int lpc, int smax) {
     const int nwarps = threads / 32, slots = threads / lpc;
     const int qpp = resident_qpp(d_pad, threads);
     return (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
-           (size_t)d_pad * sizeof(float) + (size_t)d_pad * sizeof(float4);
+           (size_t)d_pad * sizeof(float) + ((size_t)NQ * smax + NCS) * sizeof(float2);
 }
 
 laps_status choose_shape(laps_ctx* c) {
@@ -146,7 +148,7 @@ laps_status choose_shape(laps_ctx* c) {
             if (threads < 32 || threads > kMaxThreads || threads % 32) continue;
             const int cpb = threads / lpc;
             const int G = (int)((c->M + cpb - 1) / cpb);
-            const size_t smem = resident_smem(c->d_pad, threads, lpc);
+            const size_t smem = resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G));
             if (smem > 200 * 1024) continue;
             CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int bps = 0;
@@ -171,6 +173,7 @@ laps_status choose_shape(laps_ctx* c) {
     c->G = best.G;
     c->smem = best.smem;
     c->qpp = resident_qpp(c->d_pad, best.threads);
+    c->smax = resident_smax(c->d, best.G);
     c->fn = resident_fn(kind, best.lpc, best.cpl);
     return LAPS_OK;
 }
@@ -195,11 +198,11 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.sigma = c->sigma;
     P.x0 = x0;
     P.x0_scale = x0_scale;
-    P.acc = c->acc;
-    P.nacc = c->nacc;
+    P.part = c->part;
+    P.cstat = c->cstat;
+    P.ctot = c->ctot;
     P.ring = c->ring;
     P.win_sums = c->win_sums;
-    P.var_y = c->var_y;
     P.Ex2 = c->have_truth ? c->Ex2 : nullptr;
     P.inv_varx2 = c->inv_varx2;
     P.hyper = c->hyper;
@@ -234,11 +237,11 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.n_iters = n_iters;
     P.G = c->G;
     P.qpp = c->qpp;
+    P.smax = c->smax;
     P.bar_extra = g.barrier_extra_arrivals;
     P.phase_ns = c->phase_ns;
 
     CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
-    CK(cudaMemsetAsync(c->acc, 0, (size_t)3 * c->nacc * 4 * FX_STRIDE * sizeof(unsigned long long), st));
     const Coefs* cf = c->coefs;
     void* args[] = {&P, &cf};
     CK(cudaLaunchCooperativeKernel(c->fn, dim3(c->G), dim3(c->threads), args, c->smem, st));
@@ -351,12 +354,12 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
         c->allocs.push_back(*p);
         return true;
     };
-    c->nacc = NQ * c->d_pad + NCS;
     bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
               alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp_ff, M * 8) &&
               alloc((void**)&c->sigma, c->d_pad * 4) &&
-              alloc((void**)&c->acc, (size_t)3 * c->nacc * 4 * FX_STRIDE * 8) &&
-              alloc((void**)&c->var_y, c->d_pad * 4) &&
+              alloc((void**)&c->part, ((size_t)NQ * c->d_pad + NCS) * c->G * 8) &&
+              alloc((void**)&c->cstat, (size_t)c->d_pad * NCO * 4) &&
+              alloc((void**)&c->ctot, (size_t)NCS * 8) &&
               alloc((void**)&c->ring, (size_t)(c->T + 1) * c->d_pad * 8) &&
               alloc((void**)&c->win_sums, (size_t)c->d_pad * 16) &&
               alloc((void**)&c->Ex2, c->d_pad * 8) && alloc((void**)&c->inv_varx2, c->d_pad * 4) &&
@@ -431,7 +434,7 @@ laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->ring, 0, (size_t)(c->T + 1) * c->d_pad * 8, st));
     CK(cudaMemsetAsync(c->win_sums, 0, (size_t)c->d_pad * 16, st));
-    CK(cudaMemsetAsync(c->var_y, 0, c->d_pad * 4, st));
+    CK(cudaMemsetAsync(c->cstat, 0, (size_t)c->d_pad * NCO * 4, st));
     fill_kernel<<<grid_for(c->d_pad), 256, 0, st>>>(c->sigma, 1.0f, c->d_pad);
     CK(cudaGetLastError());
     // keep the caller's stream synchronous with the host copy of h above
@@ -580,7 +583,7 @@ static std::vector<std::pair<void*, size_t>> ckpt_buffers(laps_ctx* c) {
     const size_t Md = (size_t)c->M * c->d_pad;
     return {{c->y, Md * 4},           {c->u, Md * 4},          {c->g, Md * 4},
             {c->logp_ff, (size_t)c->M * 8}, {c->sigma, (size_t)c->d_pad * 4},
-            {c->var_y, (size_t)c->d_pad * 4},
+            {c->cstat, (size_t)c->d_pad * NCO * 4},
             {c->ring, (size_t)(c->T + 1) * c->d_pad * 8}, {c->win_sums, (size_t)c->d_pad * 16},
             {c->Ex2, (size_t)c->d_pad * 8},    {c->inv_varx2, (size_t)c->d_pad * 4},
             {c->hyper, sizeof(Hyper)},
@@ -646,7 +649,7 @@ laps_status laps_debug_phase_ns(laps_ctx* c, unsigned long long* out) {
     }
     if (out) {
         CK(cudaStreamSynchronize(c->last_stream));
-        CK(cudaMemcpy(out, c->phase_ns, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(out, c->phase_ns, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
         CK(cudaMemset(c->phase_ns, 0, 8 * sizeof(unsigned long long)));
     }
     return LAPS_OK;

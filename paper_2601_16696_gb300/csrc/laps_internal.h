@@ -6,7 +6,7 @@
 #include <vector>
 
 #include "laps_params.h"
-#include "laps_resident.cuh"
+#include "laps_resident_kernel.cuh"
 
 struct laps_target {
     laps_target_desc desc;
@@ -22,11 +22,12 @@ struct laps_ctx {
     // ensemble state (sampler coordinates, [M][d_pad]) and phase machine
     float *y = nullptr, *u = nullptr, *g = nullptr, *sigma = nullptr;
     float2* logp_ff = nullptr;
-    unsigned long long* acc = nullptr;
-    int nacc = 0;
+    float2* part = nullptr;   // [NQ * d_pad + NCS][G] per-block sums
+    float* cstat = nullptr;   // [d_pad][NCO] per-coordinate results
+    float2* ctot = nullptr;   // [NCS] chain totals
+    int smax = 1;             // largest coordinate slice of a block
     float2* ring = nullptr;
     float4* win_sums = nullptr;
-    float* var_y = nullptr;
     float2* Ex2 = nullptr;
     float* inv_varx2 = nullptr;
     int qpp = 1;

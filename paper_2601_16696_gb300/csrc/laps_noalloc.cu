@@ -65,10 +65,11 @@ static void carve(laps_ctx& c, laps_target& t, Carver& cv) {
     c.g = (float*)cv.take(Md * 4);
     c.logp_ff = (float2*)cv.take((size_t)c.M * 8);
     c.sigma = (float*)cv.take((size_t)c.d_pad * 4);
-    c.acc = (unsigned long long*)cv.take((size_t)3 * c.nacc * 4 * FX_STRIDE * 8);
+    c.part = (float2*)cv.take(((size_t)NQ * c.d_pad + NCS) * c.G * 8);
+    c.cstat = (float*)cv.take((size_t)c.d_pad * NCO * 4);
+    c.ctot = (float2*)cv.take((size_t)NCS * 8);
     c.ring = (float2*)cv.take((size_t)(c.T + 1) * c.d_pad * 8);
     c.win_sums = (float4*)cv.take((size_t)c.d_pad * 16);
-    c.var_y = (float*)cv.take((size_t)c.d_pad * 4);
     c.hyper = (Hyper*)cv.take(sizeof(Hyper));
     c.bar = (unsigned*)cv.take(4 * sizeof(unsigned));
     c.status = (int*)cv.take(sizeof(int));
@@ -120,7 +121,6 @@ extern "C" laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M,
     c.d_pad = t.d_pad;
     c.T = std::max(2, (int)std::ceil(cfg->window_frac * (double)cfg->n_total_steps));
     c.trace_cap = 0;  // no trace: laps_stats reports the outcome
-    c.nacc = NQ * c.d_pad + NCS;
     laps_status st = choose_shape(&c);
     if (st != LAPS_OK) return st;
     Carver count{nullptr, 0};

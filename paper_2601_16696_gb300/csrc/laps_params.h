@@ -28,6 +28,8 @@ enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4 };
 enum : int { NQ = 4 };
 enum : int { CS_DSUM = 0, CS_DSQ, CS_NFIN, CS_NBAD, CS_ASUM, NCS };
 enum : int { NCSF = 6 };  // floats per chain slot in shared memory (Delta as hi, lo)
+// per-coordinate results of the slice owners: Var y, Var x, (1 - V)^2, delta, b^2
+enum : int { CO_VARY = 0, CO_VARX, CO_DV, CO_DEL, CO_B2, NCO = 6 };
 enum : int { SL_VAR = 0, SL_DV, SL_MAXDEL, SL_B2SUM, SL_B2MAX, NSL };
 
 struct KParams {
@@ -44,11 +46,11 @@ struct KParams {
     const float* x0;    // init: [M][d] caller layout, or nullptr for Philox
     float x0_scale;
     // reduction and window state (global)
-    unsigned long long* acc;  // [3][nacc][4] fixed-point limb accumulators
-    int nacc;                 // NQ * d_pad + NCS
+    float2* part;             // [NQ * d_pad + NCS][G] per-block float-float sums
+    float* cstat;             // [d_pad][NCO] per-coordinate results of the slice owners
+    float2* ctot;             // [NCS] chain totals (written by the last block)
     float2* ring;             // [T + 1][d_pad] window values E[x_i^2] (float-float)
     float4* win_sums;         // [d_pad] running window sums (s1, s2 as float-float)
-    float* var_y;             // [d_pad] ensemble variance of the last iteration
     const float2* Ex2;        // [d_pad] truth E_p[x_i^2] (float-float) or nullptr
     const float* inv_varx2;   // [d_pad] 1 / Var_p[x_i^2]
     Hyper* hyper;
@@ -67,6 +69,7 @@ struct KParams {
     int n_iters;    // iterations of this launch
     int G;          // blocks in the grid
     int qpp;        // per-coordinate quantities reduced per shared-memory pass
+    int smax;       // largest coordinate slice of a block
     int bar_extra;  // extra arrivals every barrier waits for (test hook; 0 normally)
     unsigned long long* phase_ns;  // diagnostic build only: [5] time per phase
 };

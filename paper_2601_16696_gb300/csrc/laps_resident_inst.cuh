@@ -5,7 +5,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include "laps_resident.cuh"
+#include "laps_resident_kernel.cuh"
 
 #ifndef LAPS_INST_KIND
 #error "define LAPS_INST_KIND before including laps_resident_inst.cuh"
