@@ -85,6 +85,12 @@ void ora_normals(uint64_t seed, uint32_t m, uint32_t t, uint32_t tag, uint32_t p
     }
 }
 
+/* Diagnostic only (round_state_f32): round a vector to binary32 after a map,
+ * and form logistic-regression logits as a binary32 dot product, to measure
+ * how much binary32 arithmetic perturbs the run.  Set by ora_iterate for the
+ * duration of one iteration. */
+static int g_round_f32 = 0;
+
 /* ------------------------------------------------------------------------ */
 /* Targets.  log p up to an additive constant, and its gradient. */
 static double softplus(double z) { return (z > 0 ? z : 0.0) + log1p(exp(-fabs(z))); }
@@ -134,7 +140,13 @@ double ora_logp_grad(const ora_target* tg, const double* x, double* g) {
         for (int64_t n = 0; n < tg->n_data; ++n) {
             const double* xn = tg->X + n * d;
             double z = 0.0;
-            for (int64_t i = 0; i < d; ++i) z += xn[i] * x[i];
+            if (g_round_f32) { /* diagnostic: a binary32 dot product, in index order */
+                float zf = 0.0f;
+                for (int64_t i = 0; i < d; ++i) zf = fmaf((float)xn[i], (float)x[i], zf);
+                z = zf;
+            } else {
+                for (int64_t i = 0; i < d; ++i) z += xn[i] * x[i];
+            }
             lp += tg->y[n] * z - softplus(z);
             double r = tg->y[n] - sigmoid(z);
             for (int64_t i = 0; i < d; ++i) g[i] += r * xn[i];
@@ -222,10 +234,6 @@ int ora_integrator_coefs(int integ, double* b, double* a) {
     return 0;
 }
 
-/* Diagnostic only (round_state_f32): round a vector to binary32 after a map,
- * to measure how much a binary32 chain state perturbs the run.  Set per
- * iteration from the state's config, before the chain loop. */
-static int g_round_f32 = 0;
 static void round_f32(int64_t d, double* v) {
     if (!g_round_f32) return;
     for (int64_t i = 0; i < d; ++i) v[i] = (double)(float)v[i];
@@ -662,11 +670,19 @@ static double mams_chain(ora_state* s, int64_t m, uint32_t t0, double* z) {
     return a;
 }
 
+static int iterate_body(ora_state* s, ora_trace_row* row);
+
 int ora_iterate(ora_state* s, ora_trace_row* row) {
+    g_round_f32 = s->cfg.round_state_f32;
+    const int r = iterate_body(s, row);
+    g_round_f32 = 0;
+    return r;
+}
+
+static int iterate_body(ora_state* s, ora_trace_row* row) {
     const int64_t M = s->M, d = s->d;
     const ora_config* c = &s->cfg;
     if (s->done) return 0;
-    g_round_f32 = c->round_state_f32;
     memset(row, 0, sizeof(*row));
     row->eevpd = row->eevpd_wanted = row->dtilde = row->max_delta = row->acc = NAN;
 

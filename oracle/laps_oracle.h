@@ -105,8 +105,9 @@ typedef struct {
     int adjusted;             /* 0: stop after the unadjusted phase */
     int force_switch_at;      /* >0: switch after this many unadjusted steps */
     double fixed_eps;         /* >0: unadjusted step size held fixed (App. A, Fig. "stepsize") */
-    int round_state_f32;      /* 1: round y and u to binary32 after every map, to measure
-                                 how a binary32 chain state perturbs the run (not LAPS) */
+    int round_state_f32;      /* 1: round y and u to binary32 after every map and form
+                                 logistic-regression logits in binary32, to measure how
+                                 binary32 arithmetic perturbs the run (not LAPS) */
 } ora_config;
 
 void ora_config_default(ora_config* c);

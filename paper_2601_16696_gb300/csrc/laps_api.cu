@@ -179,9 +179,7 @@ laps_status choose_shape(laps_ctx* c) {
 }
 
 // ------------------------------------------------------------------ launch
-laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
-                            cudaStream_t st) {
-    KParams P;
+void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, KParams& P) {
     std::memset(&P, 0, sizeof(P));
     P.M = (int)c->M;
     P.d = c->d;
@@ -234,13 +232,28 @@ laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0,
     P.seed_hi = (uint32_t)(c->seed >> 32);
     P.pid = 0;
     P.mode = mode;
-    P.n_iters = n_iters;
+    P.n_iters = 1;
     P.G = c->G;
     P.qpp = c->qpp;
     P.smax = c->smax;
     P.bar_extra = g.barrier_extra_arrivals;
     P.phase_ns = c->phase_ns;
+    P.yw = c->yw;
+    P.uw = c->uw;
+    P.dlw = c->dlw;
+    P.lpw = c->lpw;
+    P.W = c->W;
+    P.gpart = c->gpart;
+    P.lpart = c->lpart;
+    P.nsplit = c->nsplit;
+    P.go = c->go;
+}
 
+laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
+                            cudaStream_t st) {
+    KParams P;
+    fill_params(c, mode, x0, x0_scale, P);
+    P.n_iters = n_iters;
     CK(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), st));
     const Coefs* cf = c->coefs;
     void* args[] = {&P, &cf};
@@ -305,7 +318,14 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
         if (!(desc->funnel_sv > 0)) return fail(LAPS_ERR_INVALID_ARG, "funnel_sv must be > 0");
         break;
     case LAPS_LOGREG:
-        return fail(LAPS_ERR_UNSUPPORTED, "LOGREG is served by the logreg entry points");
+        if (!desc->X || !desc->y || !aligned(desc->X, 4) || !aligned(desc->y, 4))
+            return fail(LAPS_ERR_INVALID_ARG, "LOGREG needs device X[n_data][d] and y[n_data]");
+        if (desc->n_data < 1 || desc->n_data > (1LL << 30))
+            return fail(LAPS_ERR_INVALID_ARG, "n_data must be in [1, 2^30]");
+        if (!(desc->prior_var > 0)) return fail(LAPS_ERR_INVALID_ARG, "prior_var must be > 0");
+        if ((d + 63) / 64 * 64 > kLogregMaxKp)
+            return fail(LAPS_ERR_UNSUPPORTED, "LOGREG is built for d <= " + std::to_string(kLogregMaxKp));
+        break;
     default:
         return fail(LAPS_ERR_INVALID_ARG, "unknown target kind");
     }
@@ -321,6 +341,28 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
         e = cudaMemcpy(t->prec_pad, desc->prec, d * sizeof(float), cudaMemcpyDeviceToDevice);
         if (e != cudaSuccess) { cudaFree(t->prec_pad); delete t; return cuda_fail(e, "copy prec"); }
     }
+    if (desc->kind == LAPS_LOGREG) {
+        // padded row stride: a multiple of 64 features for the contraction kernels
+        t->d_pad = (int)((d + 63) / 64 * 64);
+        LogregData& L = t->lr;
+        L.n = (int)desc->n_data;
+        L.d = (int)d;
+        L.kp = t->d_pad;
+        L.inv_v = (float)(1.0 / desc->prior_var);
+        const size_t xb = (size_t)L.n * L.kp * sizeof(float);
+        cudaError_t e = cudaMalloc(&L.X, xb);
+        if (e == cudaSuccess) e = cudaMalloc(&L.y, (size_t)L.n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(L.X, 0, xb);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(L.X, L.kp * sizeof(float), desc->X, d * sizeof(float), d * sizeof(float),
+                             L.n, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(L.y, desc->y, (size_t)L.n * sizeof(float), cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            laps_target_destroy(t);
+            return cuda_fail(e, "LOGREG data copy");
+        }
+    }
     *out = t;
     return LAPS_OK;
 }
@@ -328,6 +370,8 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
 void laps_target_destroy(laps_target* t) {
     if (!t) return;
     if (t->prec_pad) cudaFree(t->prec_pad);
+    if (t->lr.X) cudaFree(t->lr.X);
+    if (t->lr.y) cudaFree(t->lr.y);
     delete t;
 }
 
@@ -346,7 +390,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     c->d_pad = tg->d_pad;
     c->T = std::max(2, (int)std::ceil(cfg->window_frac * (double)cfg->n_total_steps));
     c->trace_cap = cfg->n_total_steps + 2;
-    laps_status st = choose_shape(c);
+    laps_status st = tg->kind == TGT_LOGREG ? streamed_setup(c) : choose_shape(c);
     if (st != LAPS_OK) { delete c; return st; }
     const size_t Md = (size_t)M * c->d_pad;
     auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -371,6 +415,10 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
         laps_destroy(c);
         return fail(LAPS_ERR_OOM, "device allocation of the ensemble state failed");
     }
+    if (c->streamed) {
+        st = streamed_alloc(c);
+        if (st != LAPS_OK) { laps_destroy(c); return st; }
+    }
     Coefs cf;
     coefs_table(cf);
     cudaMemcpy(c->coefs, &cf, sizeof(cf), cudaMemcpyHostToDevice);
@@ -387,6 +435,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
 void laps_destroy(laps_ctx* c) {
     if (!c) return;
     for (void* p : c->allocs) cudaFree(p);
+    if (c->h_hyper) cudaFreeHost(c->h_hyper);
     delete c;
 }
 
@@ -440,6 +489,7 @@ laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t
     // keep the caller's stream synchronous with the host copy of h above
     CK(cudaStreamSynchronize(st));
     c->initialized = true;
+    if (c->streamed) return streamed_init(c, x0, x0_scale, st);
     return launch_resident(c, 0, 1, x0, x0_scale, st);
 }
 
@@ -492,6 +542,7 @@ laps_status laps_step(laps_ctx* c, int n_iters, void* stream) {
     if (!c || n_iters < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (!c->initialized) return fail(LAPS_ERR_INVALID_ARG, "laps_init has not run");
     if (n_iters == 0) return LAPS_OK;
+    if (c->streamed) return streamed_step(c, n_iters, (cudaStream_t)stream);
     return launch_resident(c, 1, n_iters, nullptr, 0.0f, (cudaStream_t)stream);
 }
 
@@ -658,6 +709,15 @@ laps_status laps_debug_phase_ns(laps_ctx* c, unsigned long long* out) {
 
 laps_status laps_get_launch_info(const laps_ctx* c, laps_launch_info* o) {
     if (!c || !o) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    if (c->streamed) {
+        o->chains_per_block = (int)((c->M + c->seg_G - 1) / c->seg_G);
+        o->lanes_per_chain = 32;
+        o->coords_per_lane = c->seg_cpl;
+        o->threads = 256;
+        o->blocks = c->seg_G;
+        o->resident = 0;
+        return LAPS_OK;
+    }
     o->chains_per_block = c->threads / c->lpc;
     o->lanes_per_chain = c->lpc;
     o->coords_per_lane = c->cpl;

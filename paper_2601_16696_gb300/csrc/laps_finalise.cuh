@@ -1,0 +1,339 @@
+// laps_finalise.cuh -- the ensemble reductions and the finalise of one
+// Algorithm 1 iteration, shared by the register-resident kernel and the
+// streamed path.
+//
+// Input: per-block columns P.part[(q * d_pad + i) * G + b] (float-float sums
+// over block b's chains of y_i, y_i^2, g_i, y_i g_i) and per-chain sums
+// P.part[(NQ * d_pad + k) * G + b] (energy error, its square, counts,
+// acceptance).  Two steps separated by a grid-wide ordering point (a grid
+// barrier, or a kernel boundary):
+//   ens_slice   block bs of nsb reduces, in block order, the columns of its
+//               slice of coordinates and derives Var, V_ii (App. B), the
+//               window statistic delta[x_i^2] (Eq. "relative fluctuations")
+//               and b^2 (Eq. "bias"); the last block also reduces the
+//               per-chain sums;
+//   ens_gather  reads the d per-coordinate results and runs the finalise
+//               (Sec. 3.1 controller, Eq. "L", the switch of Sec. 4, the
+//               bisection of Sec. 5.1) on lane 0 of warp 0.
+// Every sum has a fixed order, so the result does not depend on timing.
+#pragma once
+#include "laps_resident.cuh"
+
+namespace laps {
+
+__device__ __forceinline__ float fmax_nan(float a, float b) { return (b > a || b != b) ? b : a; }
+
+// block-shared scratch and outputs of ens_gather
+struct FinShared {
+    ff wsum[3][kMaxThreads / 32];    // per-warp sums: Var x, (1 - V)^2, b^2
+    float wmax[2][kMaxThreads / 32];  // per-warp maxima: delta, b^2
+    int sw;                           // 1: this iteration switched to the adjusted phase
+    float eps, c1, c2s;               // step scalars of the next iteration
+    unsigned long long now;           // %globaltimer at the finalise
+};
+
+// quantities per coordinate reduced this iteration (the g sums are unused after the switch)
+__device__ __forceinline__ int ens_nq(const KParams& P, const Hyper& H) {
+    return (H.phase == 1 && P.mode == 1) ? 2 : NQ;
+}
+
+// Step 3.  s_q: shared [NQ][P.smax] + [NCS] float-float.  All threads of the block call it.
+__device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* s_q, int bs,
+                                          int nsb) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int G = P.G, dp = P.d_pad;
+    const int i0 = (int)(((long long)bs * P.d) / nsb);
+    const int i1 = (int)(((long long)(bs + 1) * P.d) / nsb);
+    const bool chain_owner = bs == nsb - 1;
+    const int nq = ens_nq(P, H);
+    const int ns = i1 - i0;
+    const bool push = (P.mode == 1 && H.phase == 0);
+    const int win_n = H.win_n;
+    // the window values this thread will update, loaded before the reductions
+    float4 w_pre = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float2 o_pre = make_float2(0.0f, 0.0f);
+    if (push && tid < ns) {
+        w_pre = P.win_sums[i0 + tid];
+        if (win_n >= P.T) o_pre = P.ring[(size_t)((win_n - P.T) % (P.T + 1)) * dp + i0 + tid];
+    }
+    // column sums over the blocks, in block order: one warp per (quantity, coordinate)
+    const int n_pairs = nq * ns + (chain_owner ? NCS : 0);
+    for (int pidx = warp; pidx < n_pairs; pidx += nwarps) {
+        size_t row;
+        if (pidx < nq * ns) row = (size_t)(pidx / ns) * dp + i0 + (pidx % ns);
+        else row = (size_t)NQ * dp + (pidx - nq * ns);
+        const float2* src = P.part + row * G;
+        ff s = ff_make(0.0f);
+        for (int c = lane; c < G; c += 32) {
+            const float2 v = __ldcg(src + c);
+            s = ff_add(s, ff{v.x, v.y});
+        }
+        s = group_sum_ff<32>(s);
+        if (lane == 0) {
+            if (pidx < nq * ns) s_q[(pidx / ns) * P.smax + (pidx % ns)] = s;
+            else s_q[NQ * P.smax + (pidx - nq * ns)] = s;
+        }
+    }
+    __syncthreads();
+    const float iM = 1.0f / (float)P.M;
+    for (int k = tid; k < ns; k += blockDim.x) {
+        const int i = i0 + k;
+        const ff mean = ff_mulf(s_q[0 * P.smax + k], iM);
+        const ff ey2 = ff_mulf(s_q[1 * P.smax + k], iM);
+        const float var_y = ff_f(ff_add(ey2, ff_neg(ff_mul(mean, mean))));
+        const float sgi = P.sigma[i];
+        const float s2i = sgi * sgi;
+        const ff ex2 = ff_mulf(ey2, s2i);
+        float dv = 0.0f, del = 0.0f, b2 = 0.0f;
+        if (nq == NQ) {
+            // V_ii = -(E[y g] - E[y] E[g])  (App. B, Eq. ECA)
+            const ff eg = ff_mulf(s_q[2 * P.smax + k], iM);
+            const ff eyg = ff_mulf(s_q[3 * P.smax + k], iM);
+            const float V = -ff_f(ff_add(eyg, ff_neg(ff_mul(mean, eg))));
+            dv = (1.0f - V) * (1.0f - V);
+        }
+        if (push) {
+            // moving window of E[x_i^2]: running sums over the last T values
+            const float4 w = k == tid ? w_pre : P.win_sums[i];
+            ff s1{w.x, w.y}, s2{w.z, w.w};
+            float2* ring_i = P.ring + i;
+            if (win_n >= P.T) {
+                const float2 o = k == tid ? o_pre : ring_i[(size_t)((win_n - P.T) % (P.T + 1)) * dp];
+                const ff old{o.x, o.y};
+                s1 = ff_add(s1, ff_neg(old));
+                s2 = ff_add(s2, ff_neg(ff_mul(old, old)));
+            }
+            s1 = ff_add(s1, ex2);
+            s2 = ff_add(s2, ff_mul(ex2, ex2));
+            P.win_sums[i] = make_float4(s1.hi, s1.lo, s2.hi, s2.lo);
+            ring_i[(size_t)(win_n % (P.T + 1)) * dp] = make_float2(ex2.hi, ex2.lo);
+            if (win_n + 1 >= P.T) {
+                const float Tf = (float)P.T;
+                const ff mu = ff_divf(s1, Tf);
+                const float vv = ff_f(ff_add(s2, ff_neg(ff_mul(s1, mu)))) / (Tf - 1.0f);
+                del = sqrtf(vv > 0.0f ? vv : 0.0f) / ff_f(mu);
+            }
+        }
+        if (P.Ex2) {
+            const float2 e = P.Ex2[i];
+            const float dd = ff_f(ff_add(ex2, ff_neg(ff{e.x, e.y})));
+            b2 = dd * dd * P.inv_varx2[i];
+        }
+        float* co = P.cstat + (size_t)i * NCO;
+        co[CO_VARY] = var_y;
+        co[CO_VARX] = s2i * var_y;
+        co[CO_DV] = dv;
+        co[CO_DEL] = del;
+        co[CO_B2] = b2;
+    }
+    if (chain_owner && tid < NCS) {
+        const ff v = s_q[NQ * P.smax + tid];
+        P.ctot[tid] = make_float2(v.hi, v.lo);
+    }
+}
+
+// Steps 4-5.  Reads the per-coordinate results (s_var receives Var y_i) and
+// the chain totals, then lane 0 of warp 0 updates H and FS.{sw, eps, c1, c2s,
+// now}.  Ends with __syncthreads(); all threads of the block call it.
+__device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_var,
+                                           FinShared& FS) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    float2 tot_pre = make_float2(0.0f, 0.0f);  // warp 0, lanes < NCS: the chain totals
+    if (warp == 0 && lane < NCS) tot_pre = __ldcg(P.ctot + lane);
+    {
+        ff a_var = ff_make(0.0f), a_dv = ff_make(0.0f), a_b2 = ff_make(0.0f);
+        float a_del = 0.0f, a_b2m = 0.0f;
+        for (int i = tid; i < P.d; i += blockDim.x) {
+            const float* co = P.cstat + (size_t)i * NCO;
+            const float vy = __ldcg(co + CO_VARY), vx = __ldcg(co + CO_VARX);
+            const float dv = __ldcg(co + CO_DV), del = __ldcg(co + CO_DEL);
+            const float b2 = __ldcg(co + CO_B2);
+            s_var[i] = vy;
+            a_var = ff_add(a_var, vx);
+            a_dv = ff_add(a_dv, dv);
+            a_b2 = ff_add(a_b2, b2);
+            a_del = fmax_nan(a_del, del);
+            a_b2m = fmax_nan(a_b2m, b2);
+        }
+        // one fused block reduction in a fixed order: warp butterflies, then warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const ff w0{__shfl_xor_sync(0xffffffffu, a_var.hi, o), __shfl_xor_sync(0xffffffffu, a_var.lo, o)};
+            const ff w1{__shfl_xor_sync(0xffffffffu, a_dv.hi, o), __shfl_xor_sync(0xffffffffu, a_dv.lo, o)};
+            const ff w3{__shfl_xor_sync(0xffffffffu, a_b2.hi, o), __shfl_xor_sync(0xffffffffu, a_b2.lo, o)};
+            a_var = ff_add(a_var, w0);
+            a_dv = ff_add(a_dv, w1);
+            a_b2 = ff_add(a_b2, w3);
+            a_del = fmax_nan(a_del, __shfl_xor_sync(0xffffffffu, a_del, o));
+            a_b2m = fmax_nan(a_b2m, __shfl_xor_sync(0xffffffffu, a_b2m, o));
+        }
+        if (lane == 0) {
+            FS.wsum[0][warp] = a_var;
+            FS.wsum[1][warp] = a_dv;
+            FS.wsum[2][warp] = a_b2;
+            FS.wmax[0][warp] = a_del;
+            FS.wmax[1][warp] = a_b2m;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // the per-warp partials combined by a butterfly over warp 0's lanes
+        ff v0 = ff_make(0.0f), v1 = v0, v3 = v0;
+        float v2 = 0.0f, v4 = 0.0f;
+        if (lane < nwarps) {
+            v0 = FS.wsum[0][lane];
+            v1 = FS.wsum[1][lane];
+            v3 = FS.wsum[2][lane];
+            v2 = FS.wmax[0][lane];
+            v4 = FS.wmax[1][lane];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const ff w0{__shfl_xor_sync(0xffffffffu, v0.hi, o), __shfl_xor_sync(0xffffffffu, v0.lo, o)};
+            const ff w1{__shfl_xor_sync(0xffffffffu, v1.hi, o), __shfl_xor_sync(0xffffffffu, v1.lo, o)};
+            const ff w3{__shfl_xor_sync(0xffffffffu, v3.hi, o), __shfl_xor_sync(0xffffffffu, v3.lo, o)};
+            v0 = ff_add(v0, w0);
+            v1 = ff_add(v1, w1);
+            v3 = ff_add(v3, w3);
+            v2 = fmax_nan(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+            v4 = fmax_nan(v4, __shfl_xor_sync(0xffffffffu, v4, o));
+        }
+        ff tot[NCS];
+#pragma unroll
+        for (int k = 0; k < NCS; ++k)
+            tot[k] = ff{__shfl_sync(0xffffffffu, tot_pre.x, k), __shfl_sync(0xffffffffu, tot_pre.y, k)};
+        if (lane == 0) {
+            Hyper h = H;  // work on a register copy
+            const float d = (float)P.d;
+            const float sum_var = ff_f(v0);
+            int sw_flag = 0;
+            if (P.mode == 0) {
+                h.eps = P.fixed_eps > 0.0f ? P.fixed_eps : P.eps0;
+                h.L = P.alpha * sqrtf(sum_var);
+                h.t0_ns = global_ns();
+            } else if (h.phase == 0) {
+                // Sec. 3.1: EEVPD, D~, desired EEVPD, new step size; Eq. "L"
+                const float nfin = ff_f(tot[CS_NFIN]), nbad = ff_f(tot[CS_NBAD]);
+                float eevpd = NAN;
+                if (nfin > 0.0f) {
+                    const ff mean = ff_divf(tot[CS_DSUM], nfin);
+                    const ff sq2 = ff_divf(tot[CS_DSQ], nfin);
+                    eevpd = ff_f(P.eevpd_centered ? ff_add(sq2, ff_neg(ff_mul(mean, mean))) : sq2) / d;
+                }
+                const float D = ff_f(v1) / d;
+                const float cd = P.C * D, rt = sqrtf(cd);
+                const float wanted = 4.0f * cd * rt / ((1.0f + rt) * (1.0f + rt));
+                h.eps_used = h.eps;
+                if (P.fixed_eps > 0.0f)
+                    h.eps = P.fixed_eps;
+                else if (nbad > 0.0f || !(eevpd > 0.0f) || !isfinite(eevpd) || !isfinite(wanted))
+                    h.eps = 0.5f * h.eps;
+                else
+                    h.eps = h.eps * powf(wanted / eevpd, 1.0f / 6.0f);
+                h.L = P.alpha * sqrtf(sum_var);
+                h.t += 1;
+                h.grads += 1;
+                h.win_n += 1;
+                h.eevpd = eevpd;
+                h.eevpd_wanted = wanted;
+                h.dtilde = D;
+                h.max_delta = (h.win_n >= P.T) ? v2 : NAN;
+                h.acc = NAN;
+                h.nonfinite_last = (int)nbad;
+                h.nonfinite_total += (int)nbad;
+                bool sw = (h.win_n >= P.T) && (v2 < P.switch_tol);
+                if (P.force_switch_at > 0) sw = h.t >= P.force_switch_at;
+                if (sw && P.adjusted && h.t < P.n_total) {
+                    sw_flag = 1;
+                    if (sum_var > 0.0f) h.eps *= sqrtf(d / sum_var);
+                    h.integ = (P.d > P.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
+                    h.a_target = (h.integ == INTEG_MN4) ? P.a_target_mn4 : P.a_target_mn2;
+                    h.L = P.adj_L_factor * P.N * h.eps;
+                    h.lo = 0.0f;
+                    h.hi = 0.0f;
+                    h.adapting = 1;
+                    h.p = 0;
+                    h.phase = 1;
+                    h.t_switch = h.t;
+                    if (h.t + P.N > P.n_total) h.done = 1;
+                } else if (h.t >= P.n_total) {
+                    h.done = 1;
+                }
+            } else {
+                // Sec. 5.1: mean acceptance, bisection until |a - a*| <= tol
+                const float a = ff_f(tot[CS_ASUM]) / (float)P.M;
+                const float nbad = ff_f(tot[CS_NBAD]);
+                h.eps_used = h.eps;
+                h.adapting = h.adapting && (fabsf(a - h.a_target) > P.acc_tol);
+                if (h.adapting) {
+                    if (a > h.a_target) {
+                        h.lo = h.eps;
+                        h.eps = (h.hi > 0.0f) ? 0.5f * (h.lo + h.hi) : 2.0f * h.eps;
+                    } else {
+                        h.hi = h.eps;
+                        h.eps = (h.lo > 0.0f) ? 0.5f * (h.lo + h.hi) : 0.5f * h.eps;
+                    }
+                }
+                h.L = P.adj_L_factor * P.N * h.eps;
+                h.acc = a;
+                h.eevpd = h.eevpd_wanted = h.dtilde = h.max_delta = NAN;
+                h.t += P.N;
+                h.p += 1;
+                h.grads += (long long)P.N * (h.integ == INTEG_MN4 ? 5 : 2);
+                h.nonfinite_last = (int)nbad;
+                h.nonfinite_total += (int)nbad;
+                if (h.t + P.N > P.n_total) h.done = 1;
+            }
+            if (P.mode == 1) h.iters += 1;
+            h.sum_var = sum_var;
+            const uint64_t now = global_ns();
+            if (P.Ex2) {
+                h.b2_avg = ff_f(v3) / d;
+                h.b2_max = v4;
+                const float b2 = P.stop_b2_max ? h.b2_max : h.b2_avg;
+                if (h.b2_first_t < 0 && b2 < 0.01f) {
+                    h.b2_first_t = h.t;
+                    h.b2_first_grads = h.grads;
+                    h.b2_first_ns = (double)(now - h.t0_ns);
+                }
+                if (P.stop_b2 > 0.0f && b2 < P.stop_b2) h.done = 1;
+            } else {
+                h.b2_avg = h.b2_max = NAN;
+            }
+            set_step_scalars(h, P.d, FS.eps, FS.c1, FS.c2s);
+            H = h;
+            FS.sw = sw_flag;
+            FS.now = now;
+        }
+    }
+    __syncthreads();
+}
+
+// the trace row of the iteration just finalised (one thread)
+__device__ __forceinline__ void ens_trace_row(const KParams& P, const Hyper& H,
+                                              unsigned long long now) {
+    if (H.iters >= P.trace_cap) return;
+    laps_trace_row r;
+    r.phase = H.phase;
+    r.t = H.t;
+    r.eps = H.eps;
+    r.L = H.L;
+    r.eps_used = P.mode == 0 ? NAN : H.eps_used;
+    r.eevpd = P.mode == 0 ? NAN : H.eevpd;
+    r.eevpd_wanted = P.mode == 0 ? NAN : H.eevpd_wanted;
+    r.dtilde = P.mode == 0 ? NAN : H.dtilde;
+    r.max_delta = P.mode == 0 ? NAN : H.max_delta;
+    r.acc = P.mode == 0 ? NAN : H.acc;
+    r.b2_max = H.b2_max;
+    r.b2_avg = H.b2_avg;
+    r.sum_var = H.sum_var;
+    r.nonfinite = P.mode == 0 ? 0 : H.nonfinite_last;
+    r.adapting = H.adapting;
+    r.grads = H.grads;
+    r.time_ns = (double)(now - H.t0_ns);
+    P.trace[H.iters] = r;
+}
+
+}  // namespace laps

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "laps_logreg.cuh"
 #include "laps_params.h"
 #include "laps_resident_kernel.cuh"
 
@@ -12,6 +13,7 @@ struct laps_target {
     laps_target_desc desc;
     int kind = 0, d = 0, d_pad = 0;
     float* prec_pad = nullptr;  // GAUSS_DIAG precisions, zero padded to d_pad (owned)
+    laps::LogregData lr{};      // LOGREG: padded copies of X and y (owned)
 };
 
 struct laps_ctx {
@@ -45,6 +47,15 @@ struct laps_ctx {
     cudaStream_t last_stream = nullptr;
     uint64_t seed = 0;
     bool initialized = false, have_truth = false;
+    // streamed path (targets whose gradient is an ensemble contraction)
+    bool streamed = false;
+    float *yw = nullptr, *uw = nullptr, *W = nullptr, *gpart = nullptr;
+    float2 *dlw = nullptr, *lpw = nullptr, *lpart = nullptr;
+    int* go = nullptr;
+    int nsplit = 1, seg_cpl = 0, seg_G = 0, fin_G = 0, adj_integ = 0;
+    size_t seg_smem = 0, fin_slice_smem = 0, fin_gather_smem = 0;
+    laps::Hyper* h_hyper = nullptr;  // pinned host copy of the phase machine (owned)
+    laps::Coefs cf{};                // integrator tables on the host
 };
 
 namespace laps {
@@ -55,6 +66,14 @@ laps_status choose_shape(laps_ctx* c);
 laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st);
 laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
                             cudaStream_t st);
+void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, KParams& P);
+// streamed path (laps_streamed.cu)
+laps_status streamed_setup(laps_ctx* c);
+laps_status streamed_alloc(laps_ctx* c);
+laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st);
+laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st);
+laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
+                                 float2* lpart, cudaStream_t st);
 laps_status status_error(int device_status);
 void stats_from_hyper(const Hyper& h, laps_stats* out);
 void coefs_table(Coefs& cf);

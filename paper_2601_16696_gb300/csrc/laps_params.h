@@ -72,6 +72,32 @@ struct KParams {
     int smax;       // largest coordinate slice of a block
     int bar_extra;  // extra arrivals every barrier waits for (test hook; 0 normally)
     unsigned long long* phase_ns;  // diagnostic build only: [5] time per phase
+    // streamed path: the state lives in global memory and the gradient comes
+    // from a separate kernel (y, u, g, logp_ff above are the accepted state)
+    float *yw, *uw;           // [M][d_pad] working position / velocity of the iteration
+    float2* dlw;              // [M] energy error of the iteration so far (float-float)
+    float2* lpw;              // [M] log p at yw (float-float)
+    float* W;                 // [M][d_pad] x = sigma o yw, the gradient kernel's input
+    const float* gpart;       // [S][M][d_pad] x-space gradient partials of the gradient kernel
+    const float2* lpart;      // [S][M] log p partials
+    int nsplit;               // S
+    int* go;                  // [2]: the iteration is live; it switched to the adjusted phase
+};
+
+// one launch of the streamed path's chain-update kernel: the maps it applies,
+// in this order, to every chain (App. E "discrete update", App. F)
+struct SegOp {
+    int phase;       // phase of the iteration this launch belongs to
+    int first;       // 1: first launch of the iteration (sets the guard, reads the accepted state)
+    int init;        // 1: draw / copy x0;  2: finish the initialisation from the gradient
+    int refresh;     // 1: full refresh u = Z / |Z| (App. F step 2, tag 3)
+    int after_grad;  // 1: take g and log p of the working point from the gradient kernel
+    float bA;        // B_{bA eps} first (0: none)
+    int o2_step;     // >= 0: O_{eps/2} of step t0 + o2_step (tag 2)
+    int o1_step;     // >= 0: O_{eps/2} of step t0 + o1_step (tag 1)
+    float bB;        // then B_{bB eps} (0: none)
+    float a;         // then A_{a eps} and write the gradient input (0: none)
+    int close;       // 1: last launch: non-finite check, MH test, keep / revert, block columns
 };
 
 }  // namespace laps

@@ -1,0 +1,558 @@
+// laps_streamed.cu -- the streamed LAPS path, for targets whose gradient is a
+// contraction over the whole ensemble (logistic regression): the chain state
+// lives in global memory (L2-resident at the sizes served) and one Algorithm 1
+// iteration is a fixed sequence of launches on one stream,
+//
+//   unadjusted step (App. E):  seg[O1 B A] grad seg[B O2 close] fin_slice fin_gather switch
+//   MAMS proposal (App. F):    seg[refresh O1 B A] (grad seg[B (O2 O1 B) A])... grad seg[B O2 close]
+//                              fin_slice fin_gather
+//
+// seg applies the maps of one stretch between two gradient evaluations to every
+// chain (a warp per chain, CPL coordinates per lane); grad is the target's
+// ensemble gradient kernel; fin_slice / fin_gather are the reduction and the
+// finalise shared with the register-resident kernel, split at a kernel
+// boundary instead of a grid barrier.  The first launch of an iteration
+// evaluates its guard (phase as expected, run not done) into go[0]; every
+// later launch of the iteration reads it, so an iteration enqueued past the
+// switch or past the end is a sequence of empty launches.  The host enqueues
+// iterations in chunks and reads the phase machine between chunks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "laps_internal.h"
+#include "laps_logreg.cuh"
+
+namespace laps {
+
+constexpr int kSegThreads = 256;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kFinThreads = 256;
+
+// ---------------------------------------------------------------- chain update
+template <int CPL>
+__global__ void __launch_bounds__(kSegThreads) seg_kernel(const KParams P, const SegOp op) {
+    constexpr int NB = CPL / 4;
+    extern __shared__ __align__(16) float seg_smem[];
+    __shared__ Hyper H;
+    __shared__ float s_eps, s_c1, s_c2s;
+    __shared__ int s_go;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dp = P.d_pad;
+    if (tid == 0) {
+        H = *P.hyper;
+        int go = 1;
+        if (op.init == 0) go = op.first ? ((!H.done && H.phase == op.phase) ? 1 : 0) : P.go[0];
+        if (op.first && blockIdx.x == 0) {
+            P.go[0] = go;
+            if (op.init) P.go[1] = 0;
+        }
+        s_go = go;
+        set_step_scalars(H, P.d, s_eps, s_c1, s_c2s);
+    }
+    __syncthreads();
+    if (!s_go) return;
+
+    const int cpb = (P.M + P.G - 1) / P.G;
+    const int mb0 = blockIdx.x * cpb, mb1 = min(P.M, mb0 + cpb);
+    const float eps = s_eps, c1 = s_c1, c2s = s_c2s;
+    const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
+    const uint32_t t0 = (uint32_t)H.t;
+    const bool columns = op.close || op.init == 2;
+
+    float sg[CPL];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        const int j = lane + 32 * k;
+        float4 s = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+        if (j < P.nblk) s = *reinterpret_cast<const float4*>(P.sigma + 4 * j);
+        sg[4 * k] = s.x; sg[4 * k + 1] = s.y; sg[4 * k + 2] = s.z; sg[4 * k + 3] = s.w;
+    }
+    float qs[NQ][CPL];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) qs[q][c] = 0.0f;
+    ff cs[NCS];
+#pragma unroll
+    for (int k = 0; k < NCS; ++k) cs[k] = ff_make(0.0f);
+
+    auto load = [&](const float* src, int64_t m, float(&v)[CPL]) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int j = lane + 32 * k;
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (j < P.nblk) a = *reinterpret_cast<const float4*>(src + (size_t)m * dp + 4 * j);
+            v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+        }
+    };
+    auto store = [&](float* dst, int64_t m, const float(&v)[CPL]) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int j = lane + 32 * k;
+            if (j < P.nblk)
+                *reinterpret_cast<float4*>(dst + (size_t)m * dp + 4 * j) =
+                    make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+    };
+    // x-space gradient partials of the gradient kernel, summed in order, to y-space
+    auto load_grad = [&](int64_t m, float(&g)[CPL], ff& lp) {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) g[q] = 0.0f;
+        lp = ff_make(0.0f);
+        for (int s = 0; s < P.nsplit; ++s) {
+            float v[CPL];
+            load(P.gpart + (size_t)s * P.M * dp, m, v);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) g[q] += v[q];
+            const float2 l = P.lpart[(size_t)s * P.M + m];
+            lp = ff_add(lp, ff{l.x, l.y});
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) g[q] *= sg[q];
+    };
+    auto store_W = [&](int64_t m, const float(&y)[CPL]) {
+        float x[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) x[q] = sg[q] * y[q];
+        store(P.W, m, x);
+    };
+
+    for (int m = mb0 + warp; m < mb1; m += kSegWarps) {
+        float y[CPL], u[CPL], g[CPL];
+        ff lp = ff_make(0.0f), dl = ff_make(0.0f);
+        if (op.init == 1) {
+            // Alg. 1 input: x0 from the caller, or x0_scale N(0, I) from the tag-0 stream
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int j = lane + 32 * k;
+                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                if (j < P.nblk && P.x0 == nullptr)
+                    normals4(j, m, 0u, TAG_X0 | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = 4 * j + c;
+                    float v = 0.0f;
+                    if (j < P.nblk && i < P.d) v = P.x0 ? P.x0[(size_t)m * P.d + i] : P.x0_scale * z[c];
+                    y[4 * k + c] = v;
+                }
+            }
+            store(P.y, m, y);
+            store_W(m, y);
+            continue;
+        }
+        if (op.init == 2) {
+            // App. C "Initialization": u0 along the gradient (a random direction if it vanishes)
+            load(P.y, m, y);
+            load_grad(m, g, lp);
+            float n2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) n2 = fmaf(g[q], g[q], n2);
+            n2 = group_sum<32>(n2);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) u[q] = 0.0f;
+            o_update<32, CPL>(P, lane, true, m, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
+            if (n2 > 0.0f) {
+                const float inv = 1.0f / sqrtf(n2);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) u[q] = g[q] * inv;
+            }
+            bool bad = !isfinite(lp.hi);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) bad = bad || !(finite_f(y[q]) && finite_f(g[q]));
+            if (bad) atomicCAS(P.status, ST_OK, ST_NONFINITE);
+            store(P.u, m, u);
+            store(P.g, m, g);
+            if (lane == 0) P.logp_ff[m] = make_float2(lp.hi, lp.lo);
+        } else {
+            load(op.first ? P.y : P.yw, m, y);
+            load(op.first ? P.u : P.uw, m, u);
+            if (op.first) {
+                load(P.g, m, g);
+                const float2 l = P.logp_ff[m];
+                lp = ff{l.x, l.y};
+            } else {
+                const float2 l = P.lpw[m], e = P.dlw[m];
+                lp = ff{l.x, l.y};
+                dl = ff{e.x, e.y};
+            }
+            if (op.after_grad) {
+                ff lpn;
+                load_grad(m, g, lpn);
+                dl = ff_add(dl, ff_neg(ff_add(lpn, ff_neg(lp))));  // -log p(x') + log p(x)
+                lp = lpn;
+            }
+            if (op.refresh) {
+                // App. F step 2: u uniform on the sphere
+                float n2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const int j = lane + 32 * k;
+                    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (j < P.nblk)
+                        normals4(j, m, (uint32_t)H.p, TAG_REFRESH | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float v = (4 * j + c < P.d) ? z[c] : 0.0f;
+                        u[4 * k + c] = v;
+                        n2 = fmaf(v, v, n2);
+                    }
+                }
+                n2 = group_sum<32>(n2);
+                const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) u[q] *= inv;
+            }
+            if (op.bA != 0.0f) b_update<32, CPL>(op.bA * eps, inv_dm1, dm1, g, u, dl);
+            if (op.o2_step >= 0) o_update<32, CPL>(P, lane, true, m, t0 + op.o2_step, TAG_O2, c1, c2s, u);
+            if (op.o1_step >= 0) o_update<32, CPL>(P, lane, true, m, t0 + op.o1_step, TAG_O1, c1, c2s, u);
+            if (op.bB != 0.0f) b_update<32, CPL>(op.bB * eps, inv_dm1, dm1, g, u, dl);
+            if (op.a != 0.0f) {
+                const float ae = op.a * eps;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) y[q] = fmaf(ae, u[q], y[q]);
+                store_W(m, y);
+            }
+            if (!op.close) {
+                store(P.yw, m, y);
+                store(P.uw, m, u);
+                if (lane == 0) {
+                    P.lpw[m] = make_float2(lp.hi, lp.lo);
+                    P.dlw[m] = make_float2(dl.hi, dl.lo);
+                }
+                continue;
+            }
+            // ---- close: non-finite check, accept / reject (App. F step 5), keep or revert
+            bool bad = !(isfinite(lp.hi) && isfinite(dl.hi));
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) bad = bad || !(finite_f(y[q]) && finite_f(u[q]) && finite_f(g[q]));
+            bad = __any_sync(0xffffffffu, bad);
+            bool keep = !bad;
+            float a_m = 0.0f;
+            if (H.phase == 1) {
+                const uint4 r = philox4x32_10(
+                    make_uint4(0u, (uint32_t)m, (uint32_t)H.p, TAG_MH | (P.pid << 8)), P.seed_lo,
+                    P.seed_hi);
+                const ff s = ff_add(dl, logf(u01(r.x)));
+                keep = !bad && (s.hi < 0.0f || (s.hi == 0.0f && s.lo < 0.0f));
+                a_m = bad ? 0.0f : (dl.hi <= 0.0f ? 1.0f : expf(-(dl.hi + dl.lo)));
+            }
+            if (keep) {
+                store(P.y, m, y);
+                store(P.u, m, u);
+                store(P.g, m, g);
+                if (lane == 0) P.logp_ff[m] = make_float2(lp.hi, lp.lo);
+            } else {
+                load(P.y, m, y);  // the accepted state stays; its values enter the sums
+                load(P.g, m, g);
+            }
+            if (H.phase == 0) {
+                if (bad) {
+                    cs[CS_NBAD] = ff_add(cs[CS_NBAD], 1.0f);
+                } else {
+                    cs[CS_DSUM] = ff_add(cs[CS_DSUM], dl);
+                    cs[CS_DSQ] = ff_add(cs[CS_DSQ], ff_f(dl) * ff_f(dl));
+                    cs[CS_NFIN] = ff_add(cs[CS_NFIN], 1.0f);
+                }
+            } else {
+                cs[CS_ASUM] = ff_add(cs[CS_ASUM], a_m);
+                if (bad) cs[CS_NBAD] = ff_add(cs[CS_NBAD], 1.0f);
+            }
+        }
+        // per-coordinate sums of y, y^2, g, y g over this warp's chains (Eq. ECA)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            qs[0][q] += y[q];
+            qs[1][q] = fmaf(y[q], y[q], qs[1][q]);
+            qs[2][q] += g[q];
+            qs[3][q] = fmaf(y[q], g[q], qs[3][q]);
+        }
+    }
+    if (!columns) return;
+
+    // ---- block columns: warps in order, float-float
+    const int nq = ens_nq(P, H);
+    float* sq = seg_smem;                                        // [NQ][warps][dp]
+    ff* scs = reinterpret_cast<ff*>(sq + (size_t)NQ * kSegWarps * dp);  // [warps][NCS]
+    for (int qd = 0; qd < nq; ++qd)
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int j = lane + 32 * k;
+            if (j < P.nblk)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sq[((size_t)qd * kSegWarps + warp) * dp + 4 * j + c] = qs[qd][4 * k + c];
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NCS; ++k) scs[warp * NCS + k] = cs[k];
+    __syncthreads();
+    const int G = P.G;
+    for (int col = tid; col < nq * dp; col += blockDim.x) {
+        const int qd = col / dp, i = col - qd * dp;
+        if (i >= P.d) continue;
+        ff s = ff_make(0.0f);
+        for (int w = 0; w < kSegWarps; ++w) s = ff_add(s, sq[((size_t)qd * kSegWarps + w) * dp + i]);
+        P.part[((size_t)qd * dp + i) * G + blockIdx.x] = make_float2(s.hi, s.lo);
+    }
+    if (tid < NCS) {
+        ff s = ff_make(0.0f);
+        for (int w = 0; w < kSegWarps; ++w) s = ff_add(s, scs[w * NCS + tid]);
+        P.part[((size_t)NQ * dp + tid) * G + blockIdx.x] = make_float2(s.hi, s.lo);
+    }
+}
+
+// ---------------------------------------------------------------- reduction and finalise
+__global__ void __launch_bounds__(kFinThreads) fin_slice_kernel(const KParams P) {
+    extern __shared__ __align__(16) float fin_smem[];
+    __shared__ Hyper H;
+    if (threadIdx.x == 0) H = *P.hyper;
+    __syncthreads();
+    if (!P.go[0]) return;
+    ens_slice(P, H, reinterpret_cast<ff*>(fin_smem), blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kFinThreads) fin_gather_kernel(const KParams P) {
+    extern __shared__ __align__(16) float fin_smem[];  // [d_pad] Var y
+    __shared__ Hyper H;
+    __shared__ FinShared FS;
+    if (threadIdx.x == 0) H = *P.hyper;
+    __syncthreads();
+    if (!P.go[0]) {
+        if (threadIdx.x == 0) P.go[1] = 0;
+        return;
+    }
+    ens_gather(P, H, fin_smem, FS);
+    if (threadIdx.x == 0) {
+        *P.hyper = H;
+        ens_trace_row(P, H, FS.now);
+        P.go[1] = FS.sw;
+    }
+    if (FS.sw)  // Sec. 4: the diagonal preconditioner, fixed from now on
+        for (int i = threadIdx.x; i < P.d; i += blockDim.x) {
+            const float v = fin_smem[i];
+            P.sigma[i] = v > 0.0f ? sqrtf(v) : 1.0f;
+        }
+}
+
+// y = x / sigma and g_y = sigma g_x of the accepted state, in the iteration that switched
+__global__ void switch_kernel(const KParams P) {
+    if (!(P.go[0] && P.go[1])) return;
+    const int64_t n = (int64_t)P.M * P.d_pad;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % P.d_pad);
+        if (i >= P.d) continue;
+        const float s = P.sigma[i];
+        P.y[k] = P.y[k] / s;
+        P.g[k] = P.g[k] * s;
+    }
+}
+
+// ---------------------------------------------------------------- host
+namespace {
+
+const void* seg_fn(int cpl) {
+    switch (cpl) {
+    case 4: return (const void*)seg_kernel<4>;
+    case 8: return (const void*)seg_kernel<8>;
+    case 16: return (const void*)seg_kernel<16>;
+    }
+    return nullptr;
+}
+
+laps_status launch_seg(laps_ctx* c, const KParams& P, const SegOp& op, cudaStream_t st) {
+    void* args[] = {const_cast<KParams*>(&P), const_cast<SegOp*>(&op)};
+    cudaError_t e = cudaLaunchKernel(seg_fn(c->seg_cpl), dim3(c->seg_G), dim3(kSegThreads), args,
+                                     c->seg_smem, st);
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "seg_kernel");
+}
+
+laps_status launch_grad(laps_ctx* c, cudaStream_t st) {
+    cudaError_t e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st);
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logreg gradient");
+}
+
+laps_status launch_fin(laps_ctx* c, const KParams& P, bool with_switch, cudaStream_t st) {
+    fin_slice_kernel<<<c->fin_G, kFinThreads, c->fin_slice_smem, st>>>(P);
+    fin_gather_kernel<<<1, kFinThreads, c->fin_gather_smem, st>>>(P);
+    if (with_switch) switch_kernel<<<std::max(1, std::min(4096, (int)((c->M * c->d_pad + 255) / 256))), 256, 0, st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "finalise kernels");
+}
+
+SegOp seg_op(int phase) {
+    SegOp o;
+    std::memset(&o, 0, sizeof(o));
+    o.phase = phase;
+    o.o2_step = -1;
+    o.o1_step = -1;
+    return o;
+}
+
+#define LCK(call)                              \
+    do {                                       \
+        laps_status s_ = (call);               \
+        if (s_ != LAPS_OK) return s_;          \
+    } while (0)
+
+// one Alg. 1 iteration of the given phase
+laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
+    KParams P;
+    fill_params(c, 1, nullptr, 0.0f, P);
+    if (phase == 0) {
+        // O_{eps/2} B_{eps/2} A_eps [grad] B_{eps/2} O_{eps/2}  (leapfrog, App. E)
+        SegOp a = seg_op(0);
+        a.first = 1;
+        a.o1_step = 0;
+        a.bB = c->cf.b[INTEG_LF][0];
+        a.a = c->cf.a[INTEG_LF][0];
+        LCK(launch_seg(c, P, a, st));
+        LCK(launch_grad(c, st));
+        SegOp b = seg_op(0);
+        b.after_grad = 1;
+        b.bA = c->cf.b[INTEG_LF][1];
+        b.o2_step = 0;
+        b.close = 1;
+        LCK(launch_seg(c, P, b, st));
+        return launch_fin(c, P, true, st);
+    }
+    // MAMS proposal: full refresh, N steps of O Phi O, accept / reject (App. F)
+    const int I = c->adj_integ, K = c->cf.K[I], N = c->cfg.steps_per_proposal;
+    SegOp a = seg_op(1);
+    a.first = 1;
+    a.refresh = 1;
+    a.o1_step = 0;
+    a.bB = c->cf.b[I][0];
+    a.a = c->cf.a[I][0];
+    LCK(launch_seg(c, P, a, st));
+    for (int n = 0; n < N; ++n) {
+        for (int s = 1; s < K - 1; ++s) {
+            LCK(launch_grad(c, st));
+            SegOp m = seg_op(1);
+            m.after_grad = 1;
+            m.bA = c->cf.b[I][s];
+            m.a = c->cf.a[I][s];
+            LCK(launch_seg(c, P, m, st));
+        }
+        LCK(launch_grad(c, st));
+        SegOp e = seg_op(1);
+        e.after_grad = 1;
+        e.bA = c->cf.b[I][K - 1];
+        e.o2_step = n;
+        if (n + 1 < N) {
+            e.o1_step = n + 1;
+            e.bB = c->cf.b[I][0];
+            e.a = c->cf.a[I][0];
+        } else {
+            e.close = 1;
+        }
+        LCK(launch_seg(c, P, e, st));
+    }
+    return launch_fin(c, P, false, st);
+}
+
+laps_status read_hyper(laps_ctx* c, cudaStream_t st, Hyper& h) {
+    cudaError_t e = cudaMemcpyAsync(c->h_hyper, c->hyper, sizeof(Hyper), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the phase machine");
+    h = *c->h_hyper;
+    return LAPS_OK;
+}
+
+}  // namespace
+
+laps_status streamed_setup(laps_ctx* c) {
+    const int dp = c->d_pad;
+    if (c->tg->kind != TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "streamed path: LOGREG only");
+    c->streamed = true;
+    c->seg_cpl = dp <= 128 ? 4 : dp <= 256 ? 8 : dp <= 512 ? 16 : 0;
+    if (c->seg_cpl == 0) return fail(LAPS_ERR_UNSUPPORTED, "streamed path: d_pad > 512");
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    // chains per block: one wave of blocks over the SMs, at least one chain per warp
+    const int64_t cpb = std::max<int64_t>(kSegWarps, (c->M + nsm - 1) / nsm);
+    c->seg_G = (int)((c->M + cpb - 1) / cpb);
+    c->G = c->seg_G;
+    c->seg_smem = (size_t)NQ * kSegWarps * dp * sizeof(float) + (size_t)kSegWarps * NCS * sizeof(ff);
+    e = cudaFuncSetAttribute(seg_fn(c->seg_cpl), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)c->seg_smem);
+    if (e != cudaSuccess) return cuda_fail(e, "seg_kernel attribute");
+    c->fin_G = std::max(1, std::min(32, c->d));
+    c->smax = (c->d + c->fin_G - 1) / c->fin_G;
+    c->fin_slice_smem = ((size_t)NQ * c->smax + NCS) * sizeof(ff);
+    c->fin_gather_smem = (size_t)dp * sizeof(float);
+    // data splits of the gradient: about two blocks of 64 chains per SM
+    const int64_t tiles = (c->M + 63) / 64;
+    c->nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * nsm + tiles - 1) / tiles));
+    c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
+    coefs_table(c->cf);
+    return LAPS_OK;
+}
+
+laps_status streamed_alloc(laps_ctx* c) {
+    const size_t Md = (size_t)c->M * c->d_pad;
+    auto alloc = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        c->allocs.push_back(*p);
+        return true;
+    };
+    bool ok = alloc((void**)&c->yw, Md * 4) && alloc((void**)&c->uw, Md * 4) &&
+              alloc((void**)&c->W, Md * 4) && alloc((void**)&c->dlw, c->M * 8) &&
+              alloc((void**)&c->lpw, c->M * 8) &&
+              alloc((void**)&c->gpart, (size_t)c->nsplit * Md * 4) &&
+              alloc((void**)&c->lpart, (size_t)c->nsplit * c->M * 8) &&
+              alloc((void**)&c->go, 4 * sizeof(int));
+    if (!ok) return fail(LAPS_ERR_OOM, "device allocation of the streamed working state failed");
+    if (cudaMallocHost((void**)&c->h_hyper, sizeof(Hyper)) != cudaSuccess)
+        return fail(LAPS_ERR_OOM, "pinned host allocation failed");
+    cudaMemset(c->W, 0, Md * 4);
+    cudaMemset(c->go, 0, 4 * sizeof(int));
+    return LAPS_OK;
+}
+
+laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st) {
+    KParams P;
+    fill_params(c, 0, x0, x0_scale, P);
+    SegOp a = seg_op(0);
+    a.first = 1;
+    a.init = 1;
+    LCK(launch_seg(c, P, a, st));
+    LCK(launch_grad(c, st));
+    SegOp b = seg_op(0);
+    b.init = 2;
+    LCK(launch_seg(c, P, b, st));
+    LCK(launch_fin(c, P, false, st));
+    c->last_stream = st;
+    return LAPS_OK;
+}
+
+laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
+    c->last_stream = st;
+    Hyper h;
+    LCK(read_hyper(c, st, h));
+    const long long target = (long long)h.iters + n_iters;
+    while (!h.done && h.iters < target) {
+        const int chunk = h.phase == 0 ? 32 : 4;
+        const int k = (int)std::min<long long>(chunk, target - h.iters);
+        for (int i = 0; i < k; ++i) LCK(enqueue_iteration(c, h.phase, st));
+        LCK(read_hyper(c, st, h));
+        int s = 0;
+        cudaError_t e = cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+        if (s != ST_OK) return status_error(s);
+    }
+    return LAPS_OK;
+}
+
+laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
+                                 float2* lpart, cudaStream_t st) {
+    cudaError_t e = logreg_grad_f32(tg->lr, W, M, 1, gpart, lpart, st);
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logreg gradient");
+}
+
+}  // namespace laps

@@ -64,6 +64,55 @@ __global__ void target_logp_grad_kernel(int kind, const float* __restrict__ x, i
     if (lane == 0) logp[m] = part.hi + part.lo;
 }
 
+// LOGREG: the caller's [M][d] points padded to the contraction layout and back
+__global__ void logreg_pack_kernel(const float* __restrict__ x, float* __restrict__ W, int64_t M,
+                                   int d, int kp) {
+    const int64_t n = M * kp;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / kp;
+        const int i = (int)(k - m * kp);
+        W[k] = i < d ? x[m * d + i] : 0.0f;
+    }
+}
+__global__ void logreg_unpack_kernel(const float* __restrict__ G, const float2* __restrict__ lp,
+                                     float* __restrict__ grad, float* __restrict__ logp, int64_t M,
+                                     int d, int kp) {
+    const int64_t n = M * d;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / d;
+        const int i = (int)(k - m * d);
+        grad[k] = G[m * kp + i];
+        if (i == 0) logp[m] = lp[m].x + lp[m].y;
+    }
+}
+
+static laps_status logreg_logp_grad(const laps_target* tg, const float* x, int64_t M, float* logp,
+                                    float* grad, cudaStream_t st) {
+    const int kp = tg->lr.kp, d = tg->d;
+    float *W = nullptr, *G = nullptr;
+    float2* lp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&W, (size_t)M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G, (size_t)M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&lp, (size_t)M * 8, st);
+    laps_status rs = LAPS_OK;
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<int64_t>((M * kp + 255) / 256, 4096);
+        logreg_pack_kernel<<<blocks, 256, 0, st>>>(x, W, M, d, kp);
+        rs = streamed_target_grad(tg, W, M, G, lp, st);
+        if (rs == LAPS_OK) {
+            logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp);
+            e = cudaGetLastError();
+        }
+    }
+    if (W) cudaFreeAsync(W, st);
+    if (G) cudaFreeAsync(G, st);
+    if (lp) cudaFreeAsync(lp, st);
+    if (rs != LAPS_OK) return rs;
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "LOGREG logp_grad");
+}
+
 }  // namespace laps
 
 using namespace laps;
@@ -71,8 +120,8 @@ using namespace laps;
 extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
                                              float* logp, float* grad, void* stream) {
     if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
-    if (tg->kind == TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "use the logreg entry points");
     if (M == 0) return LAPS_OK;
+    if (tg->kind == TGT_LOGREG) return logreg_logp_grad(tg, x, M, logp, grad, (cudaStream_t)stream);
     const int threads = 256;
     const int64_t blocks = (M * 32 + threads - 1) / threads;
     if (blocks > 0x7fffffff) return fail(LAPS_ERR_INVALID_ARG, "M too large");
