@@ -247,6 +247,7 @@ void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, K
     P.lpart = c->lpart;
     P.nsplit = c->nsplit;
     P.go = c->go;
+    P.Wb = c->mixed ? c->Wb : nullptr;
 }
 
 laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
@@ -362,6 +363,14 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
             laps_target_destroy(t);
             return cuda_fail(e, "LOGREG data copy");
         }
+        // BF16 copies for the tensor-core gradient (mixed precision); a target
+        // without them serves the FP32 form only
+        if (logreg_mma_supported(L.kp) && logreg_mma_prepare(L) != cudaSuccess) {
+            cudaGetLastError();
+            if (L.Xb) cudaFree(L.Xb);
+            if (L.Xtb) cudaFree(L.Xtb);
+            L.Xb = L.Xtb = nullptr;
+        }
     }
     *out = t;
     return LAPS_OK;
@@ -372,6 +381,8 @@ void laps_target_destroy(laps_target* t) {
     if (t->prec_pad) cudaFree(t->prec_pad);
     if (t->lr.X) cudaFree(t->lr.X);
     if (t->lr.y) cudaFree(t->lr.y);
+    if (t->lr.Xb) cudaFree(t->lr.Xb);
+    if (t->lr.Xtb) cudaFree(t->lr.Xtb);
     delete t;
 }
 
@@ -686,6 +697,7 @@ laps_status laps_restore(laps_ctx* c, const void* blob, size_t size) {
     c->seed = h.seed;
     c->have_truth = h.have_truth != 0;
     c->initialized = true;
+    c->refreshed = false;  // a mixed-precision run re-derives its FP32 g, log p if adjusted
     CK(cudaMemset(c->status, 0, sizeof(int)));
     return LAPS_OK;
 }

@@ -56,6 +56,13 @@ struct laps_ctx {
     size_t seg_smem = 0, fin_slice_smem = 0, fin_gather_smem = 0;
     laps::Hyper* h_hyper = nullptr;  // pinned host copy of the phase machine (owned)
     laps::Coefs cf{};                // integrator tables on the host
+    // mixed precision: BF16 tensor-core gradient while unadjusted
+    bool mixed = false;
+    bool refreshed = false;          // accepted g, log p recomputed in FP32 after the switch
+    void* Wb = nullptr;              // [M_pad][2 d_pad] BF16 hi | lo copy of the points
+    int64_t M_pad = 0;
+    int nsplit_mma = 1, rps_mma = 64;
+    alignas(64) unsigned char tmW[128];  // CUtensorMap of Wb
 };
 
 namespace laps {

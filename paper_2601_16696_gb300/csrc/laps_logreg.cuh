@@ -20,10 +20,30 @@ struct LogregData {
     float* X;         // [n][kp] FP32, zero padded
     float* y;         // [n] labels
     float inv_v;      // 1 / prior variance
+    // tensor-core form (kp <= 128): BF16 copies and their TMA descriptors
+    int n_pad;        // n rounded up to the 64-row chunk
+    void* Xb;         // [n_pad][kp] BF16
+    void* Xtb;        // [kp][n_pad] BF16 (X transposed)
+    alignas(64) unsigned char tmX[128];   // CUtensorMap of Xb
+    alignas(64) unsigned char tmXt[128];  // CUtensorMap of Xtb
 };
 
 // Largest padded dimension the gradient kernels take.
 constexpr int kLogregMaxKp = 256;
+
+// ---- tensor-core (tcgen05, BF16) gradient: laps_logreg_mma.cu
+bool logreg_mma_supported(int kp);
+// BF16 copies of X and their tensor maps (allocates Xb, Xtb; synchronises)
+cudaError_t logreg_mma_prepare(LogregData& D);
+// tensor map of the [M_pad][2 kp] BF16 (hi | lo) copy of the points
+cudaError_t logreg_mma_wmap(void* tmW, const void* Wb, int64_t M_pad, int kp);
+// data splits of the launch (every split non-empty) and rows per split
+int logreg_mma_splits(const LogregData& D, int64_t M, int nsm, int* rps);
+// gradient partials like logreg_grad_f32; W32 is the FP32 [M][kp] copy of the
+// points (prior terms); a bounded wait that expires sets *status
+cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W32, int64_t M, int S,
+                            int rps, float* gpart, float2* lpart, int* status, long long timeout_ns,
+                            cudaStream_t st);
 
 // log p and gradient at the M points W [M][kp] (x-space, padding columns 0),
 // with the data split into S row ranges: gpart [S][M][kp] and lpart [S][M]

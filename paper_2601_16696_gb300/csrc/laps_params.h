@@ -82,6 +82,7 @@ struct KParams {
     const float2* lpart;      // [S][M] log p partials
     int nsplit;               // S
     int* go;                  // [2]: the iteration is live; it switched to the adjusted phase
+    void* Wb;                 // mixed precision: [M_pad][2 d_pad] BF16 (hi | lo) copy of W
 };
 
 // one launch of the streamed path's chain-update kernel: the maps it applies,
@@ -89,7 +90,9 @@ struct KParams {
 struct SegOp {
     int phase;       // phase of the iteration this launch belongs to
     int first;       // 1: first launch of the iteration (sets the guard, reads the accepted state)
-    int init;        // 1: draw / copy x0;  2: finish the initialisation from the gradient
+    int init;        // 1: draw / copy x0;  2: finish the initialisation from the gradient;
+                     // 3: gradient input from the accepted state;  4: accepted g, log p from
+                     //    the gradient kernel (re-evaluation after a change of arithmetic)
     int refresh;     // 1: full refresh u = Z / |Z| (App. F step 2, tag 3)
     int after_grad;  // 1: take g and log p of the working point from the gradient kernel
     float bA;        // B_{bA eps} first (0: none)

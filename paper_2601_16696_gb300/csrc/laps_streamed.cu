@@ -16,6 +16,7 @@
 // later launch of the iteration reads it, so an iteration enqueued past the
 // switch or past the end is a sequence of empty launches.  The host enqueues
 // iterations in chunks and reads the phase machine between chunks.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -114,11 +115,29 @@ __global__ void __launch_bounds__(kSegThreads) seg_kernel(const KParams P, const
 #pragma unroll
         for (int q = 0; q < CPL; ++q) g[q] *= sg[q];
     };
+    // mixed precision, unadjusted phase: the tensor-core gradient reads x as two BF16 terms
+    const bool wb = P.Wb != nullptr && op.phase == 0 && op.init != 3;
     auto store_W = [&](int64_t m, const float(&y)[CPL]) {
         float x[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; ++q) x[q] = sg[q] * y[q];
         store(P.W, m, x);
+        if (wb) {
+            __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(P.Wb) + (size_t)m * 2 * dp;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int j = lane + 32 * k;
+                if (j >= P.nblk) continue;
+                __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    hi[c] = __float2bfloat16_rn(x[4 * k + c]);
+                    lo[c] = __float2bfloat16_rn(x[4 * k + c] - __bfloat162float(hi[c]));
+                }
+                *reinterpret_cast<uint2*>(row + 4 * j) = *reinterpret_cast<const uint2*>(hi);
+                *reinterpret_cast<uint2*>(row + dp + 4 * j) = *reinterpret_cast<const uint2*>(lo);
+            }
+        }
     };
 
     for (int m = mb0 + warp; m < mb1; m += kSegWarps) {
@@ -142,6 +161,17 @@ __global__ void __launch_bounds__(kSegThreads) seg_kernel(const KParams P, const
             }
             store(P.y, m, y);
             store_W(m, y);
+            continue;
+        }
+        if (op.init == 3) {  // re-evaluation: the accepted points as the gradient input
+            load(P.y, m, y);
+            store_W(m, y);
+            continue;
+        }
+        if (op.init == 4) {  // re-evaluation: accepted g and log p from the gradient kernel
+            load_grad(m, g, lp);
+            store(P.g, m, g);
+            if (lane == 0) P.logp_ff[m] = make_float2(lp.hi, lp.lo);
             continue;
         }
         if (op.init == 2) {
@@ -370,9 +400,16 @@ laps_status launch_seg(laps_ctx* c, const KParams& P, const SegOp& op, cudaStrea
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "seg_kernel");
 }
 
-laps_status launch_grad(laps_ctx* c, cudaStream_t st) {
-    cudaError_t e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st);
-    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logreg gradient");
+// the gradient of the working points; mma: the BF16 tensor-core form (mixed
+// precision, unadjusted phase), else FP32
+laps_status launch_grad(laps_ctx* c, bool mma, cudaStream_t st) {
+    cudaError_t e;
+    if (mma)
+        e = logreg_grad_mma(c->tg->lr, c->tmW, c->W, c->M, c->nsplit_mma, c->rps_mma, c->gpart, c->lpart,
+                            c->status, c->cfg.barrier_timeout_ns, st);
+    else
+        e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st);
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, mma ? "logreg gradient (tensor cores)" : "logreg gradient");
 }
 
 laps_status launch_fin(laps_ctx* c, const KParams& P, bool with_switch, cudaStream_t st) {
@@ -404,13 +441,14 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
     fill_params(c, 1, nullptr, 0.0f, P);
     if (phase == 0) {
         // O_{eps/2} B_{eps/2} A_eps [grad] B_{eps/2} O_{eps/2}  (leapfrog, App. E)
+        if (c->mixed) P.nsplit = c->nsplit_mma;
         SegOp a = seg_op(0);
         a.first = 1;
         a.o1_step = 0;
         a.bB = c->cf.b[INTEG_LF][0];
         a.a = c->cf.a[INTEG_LF][0];
         LCK(launch_seg(c, P, a, st));
-        LCK(launch_grad(c, st));
+        LCK(launch_grad(c, c->mixed, st));
         SegOp b = seg_op(0);
         b.after_grad = 1;
         b.bA = c->cf.b[INTEG_LF][1];
@@ -430,14 +468,14 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
     LCK(launch_seg(c, P, a, st));
     for (int n = 0; n < N; ++n) {
         for (int s = 1; s < K - 1; ++s) {
-            LCK(launch_grad(c, st));
+            LCK(launch_grad(c, false, st));
             SegOp m = seg_op(1);
             m.after_grad = 1;
             m.bA = c->cf.b[I][s];
             m.a = c->cf.a[I][s];
             LCK(launch_seg(c, P, m, st));
         }
-        LCK(launch_grad(c, st));
+        LCK(launch_grad(c, false, st));
         SegOp e = seg_op(1);
         e.after_grad = 1;
         e.bA = c->cf.b[I][K - 1];
@@ -491,11 +529,19 @@ laps_status streamed_setup(laps_ctx* c) {
     c->nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * nsm + tiles - 1) / tiles));
     c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
     coefs_table(c->cf);
+    if (c->cfg.precision == LAPS_MIXED) {
+        if (!logreg_mma_supported(dp) || c->tg->lr.Xb == nullptr)
+            return fail(LAPS_ERR_UNSUPPORTED, "mixed precision is built for LOGREG with d <= 128");
+        c->mixed = true;
+        c->M_pad = (c->M + 127) / 128 * 128;
+        c->nsplit_mma = logreg_mma_splits(c->tg->lr, c->M, nsm, &c->rps_mma);
+    }
     return LAPS_OK;
 }
 
 laps_status streamed_alloc(laps_ctx* c) {
     const size_t Md = (size_t)c->M * c->d_pad;
+    const int S = std::max(c->nsplit, c->mixed ? c->nsplit_mma : 1);
     auto alloc = [&](void** p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) return false;
         c->allocs.push_back(*p);
@@ -503,31 +549,56 @@ laps_status streamed_alloc(laps_ctx* c) {
     };
     bool ok = alloc((void**)&c->yw, Md * 4) && alloc((void**)&c->uw, Md * 4) &&
               alloc((void**)&c->W, Md * 4) && alloc((void**)&c->dlw, c->M * 8) &&
-              alloc((void**)&c->lpw, c->M * 8) &&
-              alloc((void**)&c->gpart, (size_t)c->nsplit * Md * 4) &&
-              alloc((void**)&c->lpart, (size_t)c->nsplit * c->M * 8) &&
-              alloc((void**)&c->go, 4 * sizeof(int));
+              alloc((void**)&c->lpw, c->M * 8) && alloc((void**)&c->gpart, (size_t)S * Md * 4) &&
+              alloc((void**)&c->lpart, (size_t)S * c->M * 8) && alloc((void**)&c->go, 4 * sizeof(int));
+    if (ok && c->mixed) ok = alloc(&c->Wb, (size_t)c->M_pad * 2 * c->d_pad * 2);
     if (!ok) return fail(LAPS_ERR_OOM, "device allocation of the streamed working state failed");
     if (cudaMallocHost((void**)&c->h_hyper, sizeof(Hyper)) != cudaSuccess)
         return fail(LAPS_ERR_OOM, "pinned host allocation failed");
     cudaMemset(c->W, 0, Md * 4);
     cudaMemset(c->go, 0, 4 * sizeof(int));
+    if (c->mixed) {
+        cudaMemset(c->Wb, 0, (size_t)c->M_pad * 2 * c->d_pad * 2);  // rows past M stay zero
+        cudaError_t e = logreg_mma_wmap(c->tmW, c->Wb, c->M_pad, c->d_pad);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor map of the points");
+    }
     return LAPS_OK;
 }
+
+namespace {
+// after the switch of a mixed-precision run: the accepted g and log p again in
+// FP32 (the unadjusted phase computed them on the BF16 data), so that every
+// Metropolis test compares log p of one arithmetic
+laps_status reevaluate_fp32(laps_ctx* c, cudaStream_t st) {
+    KParams P;
+    fill_params(c, 1, nullptr, 0.0f, P);
+    SegOp a = seg_op(1);
+    a.init = 3;
+    LCK(launch_seg(c, P, a, st));
+    LCK(launch_grad(c, false, st));
+    SegOp b = seg_op(1);
+    b.init = 4;
+    LCK(launch_seg(c, P, b, st));
+    c->refreshed = true;
+    return LAPS_OK;
+}
+}  // namespace
 
 laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st) {
     KParams P;
     fill_params(c, 0, x0, x0_scale, P);
+    if (c->mixed) P.nsplit = c->nsplit_mma;
     SegOp a = seg_op(0);
     a.first = 1;
     a.init = 1;
     LCK(launch_seg(c, P, a, st));
-    LCK(launch_grad(c, st));
+    LCK(launch_grad(c, c->mixed, st));
     SegOp b = seg_op(0);
     b.init = 2;
     LCK(launch_seg(c, P, b, st));
     LCK(launch_fin(c, P, false, st));
     c->last_stream = st;
+    c->refreshed = false;
     return LAPS_OK;
 }
 
@@ -535,6 +606,7 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
     c->last_stream = st;
     Hyper h;
     LCK(read_hyper(c, st, h));
+    if (c->mixed && h.phase == 1 && !c->refreshed) LCK(reevaluate_fp32(c, st));
     const long long target = (long long)h.iters + n_iters;
     while (!h.done && h.iters < target) {
         const int chunk = h.phase == 0 ? 32 : 4;
@@ -545,6 +617,7 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
         cudaError_t e = cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
         if (s != ST_OK) return status_error(s);
+        if (c->mixed && h.phase == 1 && !c->refreshed) LCK(reevaluate_fp32(c, st));
     }
     return LAPS_OK;
 }

@@ -162,6 +162,74 @@ def test_logreg_whole_run_matches_oracle(L, ora):
     assert not frozen or abs(np.mean(frozen) - 0.7) < 0.1
 
 
+# ------------------------------------------------------------------ mixed precision
+# The unadjusted phase of the mixed form evaluates the target on BF16-rounded
+# data with the tensor cores: points as two BF16 terms (about 16 significant
+# bits), residuals y - sigmoid(z) as one BF16 term, FP32 accumulation.  Its
+# reference is the FP64 oracle on the BF16-rounded data; the error bars below
+# are the arithmetic's, stated with the result.
+
+def _bf16_round(X):
+    return torch.from_numpy(np.asarray(X, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+@pytest.mark.parametrize("n,nf,M", [(1000, 100, 300), (77, 5, 129), (3000, 120, 8192),
+                                    (64, 63, 2), (10000, 100, 256)])
+def test_mixed_gradient_vs_oracle_on_bf16_data(L, ora, n, nf, M):
+    pr = W.logreg(n_data=n, n_feat=nf, M=M, n_steps=10)
+    s = _gpu(L, pr, seed=0, precision=1)
+    _, _, g, lp, _ = s.state()
+    ot = ora.OracleTarget(pr.kind, pr.d, X=_bf16_round(pr.X), y=pr.y, prior_var=pr.prior_var)
+    lpr, gr = ot.logp_grad(pr.x0.astype(np.float64))
+    g = g.double().cpu().numpy()
+    scale = np.abs(gr).max(axis=1, keepdims=True)
+    err_g = np.max(np.abs(g - gr) / scale)
+    # one BF16 rounding of each residual (relative 2^-9), averaged over the rows
+    assert err_g < 4e-3, err_g
+    err_lp = np.max(np.abs(lp.cpu().numpy() - lpr) / (np.abs(lpr) + 1.0))
+    assert err_lp < 2e-5, err_lp
+
+
+def test_mixed_first_steps_error_stated(L, ora):
+    pr = W.logreg(n_data=1000, M=512, n_steps=200)
+    s = _gpu(L, pr, seed=3, fixed_eps=0.01, precision=1)
+    ot = ora.OracleTarget(pr.kind, pr.d, X=_bf16_round(pr.X), y=pr.y, prior_var=pr.prior_var)
+    r = ora.OracleLAPS(ot, pr.x0, seed=3, n_total_steps=pr.n_steps, fixed_eps=0.01)
+    errs = []
+    for _ in range(10):
+        s.step(1)
+        r.iterate(1)
+        errs.append(_rel(s.sample().double().cpu().numpy(), r.x()))
+    assert max(errs) < 1e-4, errs
+
+
+def test_mixed_whole_run_matches_fp32(L, ora):
+    pr = W.logreg(n_data=1000, M=512, n_steps=400)
+    cfg = dict(force_switch_at=100)
+    a = _gpu(L, pr, seed=0, precision=1, **cfg)
+    a.run()
+    b = _gpu(L, pr, seed=0, precision=0, **cfg)
+    b.run()
+    sa, sb = a.stats(), b.stats()
+    assert sa["t"] == sb["t"] and sa["t_switch"] == sb["t_switch"] == 100
+    xa, xb = a.sample().double().cpu().numpy(), b.sample().double().cpu().numpy()
+    m2a, m2b, v2b = (xa ** 2).mean(0), (xb ** 2).mean(0), (xb ** 2).var(0)
+    assert float(np.mean((m2a - m2b) ** 2 / v2b)) < 10.0 / pr.M
+    # the adjusted phase tests log p of one arithmetic: acceptance is sane from the first proposal
+    rows = [r for r in a.trace() if r["phase"] == 1 and r["acc"] == r["acc"]]
+    assert rows[0]["acc"] > 0.5, rows[0]
+    frozen = [r["acc"] for r in rows if not r["adapting"]]
+    assert not frozen or abs(np.mean(frozen) - 0.7) < 0.1
+
+
+def test_mixed_rejects_unbuilt_shapes(L):
+    pr = W.logreg(n_data=200, n_feat=150, M=64, n_steps=10)  # d = 151 -> kp = 192
+    tg = L.Target.from_problem(pr)
+    with pytest.raises(L.LapsError) as e:
+        L.Sampler(tg, pr.M, n_total_steps=10, precision=1)
+    assert e.value.status == 6
+
+
 def test_logreg_determinism_and_checkpoint(L):
     pr = W.logreg(n_data=500, n_feat=30, M=200, n_steps=200)
     outs = []
