@@ -697,7 +697,10 @@ laps_status laps_restore(laps_ctx* c, const void* blob, size_t size) {
     c->seed = h.seed;
     c->have_truth = h.have_truth != 0;
     c->initialized = true;
-    c->refreshed = false;  // a mixed-precision run re-derives its FP32 g, log p if adjusted
+    // a checkpoint is taken between laps_step calls, after the switch's one-time work
+    Hyper hh;
+    CK(cudaMemcpy(&hh, c->hyper, sizeof(hh), cudaMemcpyDeviceToHost));
+    c->refreshed = hh.phase == 1;
     CK(cudaMemset(c->status, 0, sizeof(int)));
     return LAPS_OK;
 }

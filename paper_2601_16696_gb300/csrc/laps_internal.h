@@ -58,7 +58,7 @@ struct laps_ctx {
     laps::Coefs cf{};                // integrator tables on the host
     // mixed precision: BF16 tensor-core gradient while unadjusted
     bool mixed = false;
-    bool refreshed = false;          // accepted g, log p recomputed in FP32 after the switch
+    bool refreshed = false;          // streamed: the switch's one-time work is done
     void* Wb = nullptr;              // [M_pad][2 d_pad] BF16 hi | lo copy of the points
     int64_t M_pad = 0;
     int nsplit_mma = 1, rps_mma = 64;

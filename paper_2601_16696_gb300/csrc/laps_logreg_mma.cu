@@ -33,9 +33,9 @@ namespace {
 constexpr int MT = 128;      // chains per CTA (MMA M)
 constexpr int TNR = 64;      // data rows per chunk (MMA N of Z, K of G)
 constexpr int NSTAGE = 3;    // X / X^T ring depth
-constexpr int NTHR = 384;
+constexpr int NTHR = 640;
 constexpr int EPI_WARP0 = 4;  // first epilogue warp
-constexpr int NEPI = 8;       // epilogue warps
+constexpr int NEPI = 16;      // epilogue warps: 4 lane quarters x 4 column quarters
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -113,6 +113,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 // Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
 // layout (rows of 128 bytes, 8-row groups 1024 bytes apart), start address
 // at a 16-byte step inside a 1024-byte aligned atom.
@@ -158,8 +173,8 @@ struct Smem {
     static constexpr uint32_t OFF_X = OFF_W + W_BYTES;
     static constexpr uint32_t OFF_R = OFF_X + NSTAGE * STAGE;
     static constexpr uint32_t OFF_BAR = OFF_R + 2 * R_BYTES;
-    static constexpr uint32_t OFF_LP = OFF_BAR + 256;      // [MT] float-float
-    static constexpr uint32_t TOTAL = OFF_LP + MT * 8 + 1024;  // + alignment slack
+    static constexpr uint32_t OFF_LP = OFF_BAR + 256;      // [4][MT] float-float
+    static constexpr uint32_t TOTAL = OFF_LP + 4 * MT * 8 + 1024;  // + alignment slack
     static constexpr uint32_t TMEM_COLS = 2 * TNR + KP <= 256 ? 256 : 512;
 };
 
@@ -305,7 +320,7 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
     } else if (warp >= EPI_WARP0 && warp < EPI_WARP0 + NEPI) {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;                 // TMEM lane quarter: chains 32q .. 32q+31
-        const int h = (warp - EPI_WARP0) >> 2;  // column half
+        const int h = (warp - EPI_WARP0) >> 2;  // column quarter: Z columns 16h .. 16h+15
         const int rt = 32 * q + lane;           // this thread's chain in the tile
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
         ff lp = ff_make(0.0f);
@@ -314,47 +329,57 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
             const int zb = c & 1;
             if (!mbar_wait(bar(B_ZFULL + zb), (c >> 1) & 1, deadline)) { ok = false; break; }
             tc_fence_after();
-            float z[32];
-            tmem_ld32(tZ + lane_off + (uint32_t)(zb * TNR + 32 * h), z);
+            float z[16];
+            tmem_ld16(tZ + lane_off + (uint32_t)(zb * TNR + 16 * h), z);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_ZEMPTY + zb));
-            // residuals and log-likelihood terms of data rows row0 .. row0 + 31
-            const int row0 = r_begin + c * TNR + 32 * h;
-            float r[32];
+            // residuals and log-likelihood terms of data rows row0 .. row0 + 15.  Fast
+            // intrinsics (this form serves the unadjusted phase only): t = e^{-|z|},
+            // sigmoid from 1 / (1 + t), softplus = max(z, 0) + log(1 + t)
+            const int row0 = r_begin + c * TNR + 16 * h;
+            const int nlive = min(16, r_end - row0);
+            float r[16];
             float lsum = 0.0f;
+            auto body = [&](auto full) {
+                float yy[16];
+                if (decltype(full)::value) {
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-                float4 yv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (row0 + 4 * j4 + 3 < r_end) yv = __ldg(reinterpret_cast<const float4*>(A.y + row0) + j4);
-                else {
-                    float t4[4];
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float4 v = __ldg(reinterpret_cast<const float4*>(A.y + row0) + j4);
+                        yy[4 * j4] = v.x; yy[4 * j4 + 1] = v.y; yy[4 * j4 + 2] = v.z; yy[4 * j4 + 3] = v.w;
+                    }
+                } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) t4[e] = (row0 + 4 * j4 + e < r_end) ? A.y[row0 + 4 * j4 + e] : 0.0f;
-                    yv = make_float4(t4[0], t4[1], t4[2], t4[3]);
+                    for (int j = 0; j < 16; ++j) yy[j] = j < nlive ? A.y[row0 + j] : 0.0f;
                 }
-                const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = 4 * j4 + e;
-                    const bool live = row0 + j < r_end;
+                for (int j = 0; j < 16; ++j) {
                     const float zz = z[j];
                     const float t = __expf(-fabsf(zz));
-                    const float sp = fmaxf(zz, 0.0f) + log1pf(t);
-                    const float inv = __frcp_rn(1.0f + t);
+                    const float opt = 1.0f + t;
+                    const float inv = __fdividef(1.0f, opt);
                     const float sig = zz >= 0.0f ? inv : t * inv;
-                    r[j] = live ? yy[e] - sig : 0.0f;
-                    lsum += live ? fmaf(yy[e], zz, -sp) : 0.0f;
+                    const float term = fmaf(yy[j], zz, -(fmaxf(zz, 0.0f) + __logf(opt)));
+                    if (decltype(full)::value) {
+                        r[j] = yy[j] - sig;
+                        lsum += term;
+                    } else {
+                        r[j] = j < nlive ? yy[j] - sig : 0.0f;
+                        lsum += j < nlive ? term : 0.0f;
+                    }
                 }
-            }
+            };
+            if (nlive >= 16) body(std::true_type{});
+            else body(std::false_type{});
             lp = ff_add(lp, lsum);
             const int rb = zb;
             if (!mbar_wait(bar(B_REMPTY + rb), ((c >> 1) & 1) ^ 1, deadline)) { ok = false; break; }
-            // R row rt, 16-byte chunks 4h .. 4h+3 of the 128-byte row, 128-byte swizzle
+            // R row rt, 16-byte chunks 2h, 2h+1 of the 128-byte row, 128-byte swizzle
             unsigned char* rrow = gbase + S::OFF_R + (size_t)rb * S::R_BYTES + (size_t)rt * 128;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int chunk = (4 * h + t) ^ (rt & 7);
+            for (int t = 0; t < 2; ++t) {
+                const int chunk = (2 * h + t) ^ (rt & 7);
                 uint4 v;
                 v.x = pack_bf16(r[8 * t + 0], r[8 * t + 1]);
                 v.y = pack_bf16(r[8 * t + 2], r[8 * t + 3]);
@@ -373,19 +398,19 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
         if (!ok) atomicExch(&s_fail, 1);
         if (ok) {
             tc_fence_after();
-            // G columns [h kp/2, (h+1) kp/2) of chain m, plus the prior on split 0
+            // G columns [h kp/4, (h+1) kp/4) of chain m, plus the prior on split 0
             float* gout = A.gpart + ((size_t)split * A.M + (m < A.M ? m : 0)) * KP;
 #pragma unroll
             for (int piece = 0; piece < KP / 64; ++piece) {
-                float g[32];
-                const int col = h * (KP / 2) + 32 * piece;
-                tmem_ld32(tG + lane_off + (uint32_t)col, g);
+                float g[16];
+                const int col = h * (KP / 4) + 16 * piece;
+                tmem_ld16(tG + lane_off + (uint32_t)col, g);
                 if (nc == 0)
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) g[k] = 0.0f;  // no chunk: G was never written
+                    for (int k = 0; k < 16; ++k) g[k] = 0.0f;  // no chunk: G was never written
                 if (m < A.M) {
 #pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
+                    for (int j4 = 0; j4 < 4; ++j4) {
                         float4 v = make_float4(g[4 * j4], g[4 * j4 + 1], g[4 * j4 + 2], g[4 * j4 + 3]);
                         if (split == 0) {
                             const float4 w = *reinterpret_cast<const float4*>(wrow + col + 4 * j4);
@@ -398,13 +423,15 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
                     }
                 }
             }
-            // log p: the two column halves of a chain meet in shared memory
-            if (h == 1) s_lp[rt] = lp;
+            // log p: the four column quarters of a chain meet in shared memory
+            s_lp[h * MT + rt] = lp;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(NEPI * 32) : "memory");  // every epilogue warp
         if (ok) {
             if (h == 0 && m < A.M) {
-                ff l = ff_add(lp, s_lp[rt]);
+                ff l = s_lp[rt];
+#pragma unroll
+                for (int k = 1; k < 4; ++k) l = ff_add(l, s_lp[k * MT + rt]);
                 if (split == 0) {
                     float w2 = 0.0f;
                     for (int k = 0; k < KP; k += 4) {

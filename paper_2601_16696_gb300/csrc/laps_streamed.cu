@@ -35,7 +35,7 @@ constexpr int kFinThreads = 256;
 
 // ---------------------------------------------------------------- chain update
 template <int CPL>
-__global__ void __launch_bounds__(kSegThreads) seg_kernel(const KParams P, const SegOp op) {
+__global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(const KParams P, const SegOp op) {
     constexpr int NB = CPL / 4;
     extern __shared__ __align__(16) float seg_smem[];
     __shared__ Hyper H;
@@ -335,30 +335,32 @@ __global__ void __launch_bounds__(kSegThreads) seg_kernel(const KParams P, const
 }
 
 // ---------------------------------------------------------------- reduction and finalise
-__global__ void __launch_bounds__(kFinThreads) fin_slice_kernel(const KParams P) {
+// One launch: every block reduces its slice of coordinates (ens_slice); the
+// last block to finish, found by a ticket counter (no block waits for
+// another), gathers and runs the finalise (ens_gather).
+__global__ void __launch_bounds__(kFinThreads) fin_kernel(const KParams P) {
+    // slice: [NQ smax + NCS] float-float; then, in the last block, [d_pad] Var y
     extern __shared__ __align__(16) float fin_smem[];
     __shared__ Hyper H;
+    __shared__ FinShared FS;
+    __shared__ unsigned s_ticket;
+    unsigned* count = reinterpret_cast<unsigned*>(P.go + 2);
     if (threadIdx.x == 0) H = *P.hyper;
     __syncthreads();
     if (!P.go[0]) return;
     ens_slice(P, H, reinterpret_cast<ff*>(fin_smem), blockIdx.x, gridDim.x);
-}
-
-__global__ void __launch_bounds__(kFinThreads) fin_gather_kernel(const KParams P) {
-    extern __shared__ __align__(16) float fin_smem[];  // [d_pad] Var y
-    __shared__ Hyper H;
-    __shared__ FinShared FS;
-    if (threadIdx.x == 0) H = *P.hyper;
+    __threadfence();
     __syncthreads();
-    if (!P.go[0]) {
-        if (threadIdx.x == 0) P.go[1] = 0;
-        return;
-    }
+    if (threadIdx.x == 0) s_ticket = atomicAdd(count, 1u);
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1) return;
+    __threadfence();
     ens_gather(P, H, fin_smem, FS);
     if (threadIdx.x == 0) {
         *P.hyper = H;
         ens_trace_row(P, H, FS.now);
         P.go[1] = FS.sw;
+        *count = 0u;  // ready for the next launch
     }
     if (FS.sw)  // Sec. 4: the diagonal preconditioner, fixed from now on
         for (int i = threadIdx.x; i < P.d; i += blockDim.x) {
@@ -367,9 +369,8 @@ __global__ void __launch_bounds__(kFinThreads) fin_gather_kernel(const KParams P
         }
 }
 
-// y = x / sigma and g_y = sigma g_x of the accepted state, in the iteration that switched
-__global__ void switch_kernel(const KParams P) {
-    if (!(P.go[0] && P.go[1])) return;
+// Sec. 4, once after the switch: y = x / sigma and g_y = sigma g_x of the accepted state
+__global__ void precondition_kernel(const KParams P) {
     const int64_t n = (int64_t)P.M * P.d_pad;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -412,12 +413,10 @@ laps_status launch_grad(laps_ctx* c, bool mma, cudaStream_t st) {
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, mma ? "logreg gradient (tensor cores)" : "logreg gradient");
 }
 
-laps_status launch_fin(laps_ctx* c, const KParams& P, bool with_switch, cudaStream_t st) {
-    fin_slice_kernel<<<c->fin_G, kFinThreads, c->fin_slice_smem, st>>>(P);
-    fin_gather_kernel<<<1, kFinThreads, c->fin_gather_smem, st>>>(P);
-    if (with_switch) switch_kernel<<<std::max(1, std::min(4096, (int)((c->M * c->d_pad + 255) / 256))), 256, 0, st>>>(P);
+laps_status launch_fin(laps_ctx* c, const KParams& P, cudaStream_t st) {
+    fin_kernel<<<c->fin_G, kFinThreads, std::max(c->fin_slice_smem, c->fin_gather_smem), st>>>(P);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "finalise kernels");
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "finalise kernel");
 }
 
 SegOp seg_op(int phase) {
@@ -455,7 +454,7 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
         b.o2_step = 0;
         b.close = 1;
         LCK(launch_seg(c, P, b, st));
-        return launch_fin(c, P, true, st);
+        return launch_fin(c, P, st);
     }
     // MAMS proposal: full refresh, N steps of O Phi O, accept / reject (App. F)
     const int I = c->adj_integ, K = c->cf.K[I], N = c->cfg.steps_per_proposal;
@@ -489,7 +488,7 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
         }
         LCK(launch_seg(c, P, e, st));
     }
-    return launch_fin(c, P, false, st);
+    return launch_fin(c, P, st);
 }
 
 laps_status read_hyper(laps_ctx* c, cudaStream_t st, Hyper& h) {
@@ -512,15 +511,15 @@ laps_status streamed_setup(laps_ctx* c) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
-    // chains per block: one wave of blocks over the SMs, at least one chain per warp
-    const int64_t cpb = std::max<int64_t>(kSegWarps, (c->M + nsm - 1) / nsm);
-    c->seg_G = (int)((c->M + cpb - 1) / cpb);
+    // one chain per warp: a chain update is a chain of dependent reductions and
+    // Philox rounds, so the kernel wants many chains in flight, not long loops
+    c->seg_G = (int)((c->M + kSegWarps - 1) / kSegWarps);
     c->G = c->seg_G;
     c->seg_smem = (size_t)NQ * kSegWarps * dp * sizeof(float) + (size_t)kSegWarps * NCS * sizeof(ff);
     e = cudaFuncSetAttribute(seg_fn(c->seg_cpl), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)c->seg_smem);
     if (e != cudaSuccess) return cuda_fail(e, "seg_kernel attribute");
-    c->fin_G = std::max(1, std::min(32, c->d));
+    c->fin_G = std::max(1, std::min(2 * nsm, c->d));
     c->smax = (c->d + c->fin_G - 1) / c->fin_G;
     c->fin_slice_smem = ((size_t)NQ * c->smax + NCS) * sizeof(ff);
     c->fin_gather_smem = (size_t)dp * sizeof(float);
@@ -579,6 +578,21 @@ laps_status reevaluate_fp32(laps_ctx* c, cudaStream_t st) {
     SegOp b = seg_op(1);
     b.init = 4;
     LCK(launch_seg(c, P, b, st));
+    return LAPS_OK;
+}
+
+// the one-time work of the switch, enqueued by the host once it reads the new
+// phase (the iterations enqueued after the switching one are empty): the
+// accepted state into preconditioned coordinates, then, for the mixed form,
+// its g and log p again in FP32
+laps_status after_switch(laps_ctx* c, cudaStream_t st) {
+    KParams P;
+    fill_params(c, 1, nullptr, 0.0f, P);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (c->M * c->d_pad + 255) / 256));
+    precondition_kernel<<<blocks, 256, 0, st>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "precondition_kernel");
+    if (c->mixed) LCK(reevaluate_fp32(c, st));
     c->refreshed = true;
     return LAPS_OK;
 }
@@ -596,7 +610,7 @@ laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStre
     SegOp b = seg_op(0);
     b.init = 2;
     LCK(launch_seg(c, P, b, st));
-    LCK(launch_fin(c, P, false, st));
+    LCK(launch_fin(c, P, st));
     c->last_stream = st;
     c->refreshed = false;
     return LAPS_OK;
@@ -606,7 +620,7 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
     c->last_stream = st;
     Hyper h;
     LCK(read_hyper(c, st, h));
-    if (c->mixed && h.phase == 1 && !c->refreshed) LCK(reevaluate_fp32(c, st));
+    if (h.phase == 1 && !c->refreshed) LCK(after_switch(c, st));
     const long long target = (long long)h.iters + n_iters;
     while (!h.done && h.iters < target) {
         const int chunk = h.phase == 0 ? 32 : 4;
@@ -617,7 +631,7 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
         cudaError_t e = cudaMemcpy(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
         if (s != ST_OK) return status_error(s);
-        if (c->mixed && h.phase == 1 && !c->refreshed) LCK(reevaluate_fp32(c, st));
+        if (h.phase == 1 && !c->refreshed) LCK(after_switch(c, st));
     }
     return LAPS_OK;
 }
