@@ -249,6 +249,59 @@ typedef struct {
 } laps_launch_info;
 laps_status laps_get_launch_info(const laps_ctx* ctx, laps_launch_info* out);
 
+/* ---- many problems in one launch -----------------------------------------
+ * A batch of independent diagonal-Gaussian problems of uneven dimension and
+ * ensemble size (the paper runs one problem per call; batching is this
+ * library's: Alg. 1 runs for every problem in lockstep iterations inside one
+ * persistent cooperative launch).  Problem k draws from the Philox stream of
+ * the batch seed with problem id pid = k, so it reproduces a single-problem
+ * run of the same seed and pid up to the order of the ensemble sums.  The
+ * state streams from device memory (y and u per chain; the gradient and the
+ * energy error are recomputed), so any d up to 10240 is served. */
+typedef struct laps_batch laps_batch;
+typedef struct {
+    int64_t d;              /* dimension, 2 .. 10240 */
+    int64_t M;              /* chains, >= 2 */
+    const float* prec;      /* device [d]: precisions 1/sigma_i^2 (copied) */
+    const float* x0;        /* device [M][d] initial positions (read at laps_batch_init),
+                               or NULL for x0_scale N(0, I) from the Philox tag-0 stream */
+    double x0_scale;
+} laps_problem;
+
+/* Shape of the persistent launch: coordinates per lane (8, 12, 16, 20),
+ * warps per chain widened 2^widen times beyond the smallest that holds d,
+ * coordinates per reduction slice task.  laps_batch_tune sets it. */
+typedef struct {
+    int coords_per_lane, widen, slice;
+    int threads, blocks;    /* read only */
+    int tuned;              /* 1 once laps_batch_tune chose it */
+} laps_batch_shape;
+
+/* Allocates every problem's state with cfg (n_total_steps, N, ... shared). */
+laps_status laps_batch_create(const laps_problem* probs, int n, const laps_config* cfg,
+                              laps_batch** out);
+void laps_batch_destroy(laps_batch* b);
+/* Truth for problem k's b^2 (host [d] arrays, as laps_set_truth). */
+laps_status laps_batch_set_truth(laps_batch* b, int k, const double* Ex2, const double* Varx2);
+/* Initialises every problem (Alg. 1 first lines); one launch. */
+laps_status laps_batch_init(laps_batch* b, uint64_t seed, void* stream);
+/* Up to n_iters lockstep iterations in one persistent launch (a problem that
+ * finished idles).  Capturable in a CUDA graph. */
+laps_status laps_batch_step(laps_batch* b, int n_iters, void* stream);
+/* Runs every problem to its end: a CUDA graph of one launch of
+ * iters_per_launch iterations, replayed until all problems are done. */
+laps_status laps_batch_run(laps_batch* b, int iters_per_launch, void* stream);
+/* Autotuner: times every feasible shape for two iterations from the current
+ * state (restored afterwards) and keeps the fastest; synchronises. */
+laps_status laps_batch_tune(laps_batch* b, void* stream);
+laps_status laps_batch_get_shape(const laps_batch* b, laps_batch_shape* out);
+laps_status laps_batch_set_shape(laps_batch* b, const laps_batch_shape* shape);
+/* Per problem, as the single-problem calls (these synchronise). */
+laps_status laps_batch_get_stats(laps_batch* b, int k, laps_stats* out);
+laps_status laps_batch_get_trace(laps_batch* b, int k, laps_trace_row* rows, int cap, int* n);
+/* Problem k's chain positions x = sigma o y: x_out device [M_k][d_k]. */
+laps_status laps_batch_sample(laps_batch* b, int k, float* x_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -470,7 +470,7 @@ laps_status laps_set_truth(laps_ctx* c, const double* Ex2, const double* Varx2) 
 
 namespace laps {
 // the phase machine before Alg. 1's first line
-static Hyper initial_hyper() {
+Hyper initial_hyper() {
     Hyper h;
     std::memset(&h, 0, sizeof(h));
     h.phase = 0;

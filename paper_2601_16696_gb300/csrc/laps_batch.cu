@@ -1,0 +1,587 @@
+// laps_batch.cu -- many independent LAPS problems (diagonal Gaussians of
+// uneven dimension and ensemble size) in one persistent cooperative launch.
+//
+// The batch is too large for register residency (a d = 10^4 problem with
+// 16384 chains alone is 1.3 GB of y and u), so the state streams from HBM:
+// an unadjusted step reads and writes y and u once (16 bytes per coordinate);
+// g and the energy error are recomputed from y (g = -prec o x, Eq. ECA's
+// statistics need only sums of y and y^2 per coordinate for this target).
+//
+// A launch runs iterations of Algorithm 1 for every live problem in lockstep:
+//   1. chain phase: every block takes the same share (1/G) of every problem's
+//      chains, so blocks stay balanced whatever phase each problem is in.  A
+//      chain is processed by a group of gw warps (gw = 1..16, chosen per
+//      problem from its d), with its coordinates in registers (CPL per lane)
+//      and group reductions by warp butterflies plus, across the group's
+//      warps, shared memory and a named barrier.  Per-coordinate sums of y
+//      and y^2 accumulate in shared memory per thread; the block writes one
+//      float-float column per problem (the register-resident kernel's layout);
+//   2. grid barrier; slice tasks (problem, block of coordinates) spread over
+//      the blocks run ens_slice;
+//   3. grid barrier; the finalise of problem p runs on block p mod G;
+//   4. grid barrier.
+// All sums have fixed orders; a result depends on the launch shape (the block
+// and group counts fix the order of the column sums), not on timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "laps_internal.h"
+
+namespace laps {
+
+constexpr int kBT = 512;          // threads per block
+constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kRed = 128;         // reduction scratch floats per group: 2 buffers x 16 warps x 4
+
+struct BatchArgs {
+    const KParams* probs;  // [n]
+    const int* gw;         // [n] warps per chain
+    const Coefs* coefs;
+    int n;                 // problems
+    int mode;              // 0: initialise, 1: iterate
+    int n_iters;
+    int SL;                // coordinates per slice task
+    int cap_pad;           // shared capacity of the per-coordinate constants (>= every d_pad)
+    unsigned* bar_count;
+    int* status;
+    long long timeout_ns;
+    int bar_extra;
+};
+
+// ---------------------------------------------------------------- chain groups
+struct Grp {
+    int gw;      // warps in the group
+    int grp;     // group index in the block
+    int wig;     // warp in the group
+    int gl;      // lane in the group (0 .. 32 gw - 1)
+    int lpc;     // lanes per chain = 32 gw
+    float* red;  // this group's reduction scratch
+    int flip;    // scratch buffer in use
+};
+
+__device__ __forceinline__ void grp_bar(const Grp& G) {
+    if (G.gw > 1) asm volatile("bar.sync %0, %1;" ::"r"(1 + G.grp), "r"(32 * G.gw) : "memory");
+}
+
+// Sum of NV values over the group: warp butterfly, then the group's warps in
+// order.  Two scratch buffers alternate, so one barrier per call suffices (a
+// warp cannot run two calls ahead of the others).  Every lane gets the same bits.
+template <int NV>
+__device__ __forceinline__ void gsum(Grp& G, float (&v)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (G.gw == 1) return;
+    float* s = G.red + G.flip * 64;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[G.wig * 4 + k] = v[k];
+    grp_bar(G);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float t = s[k];
+        for (int w = 1; w < G.gw; ++w) t += s[w * 4 + k];
+        v[k] = t;
+    }
+    G.flip ^= 1;
+}
+__device__ __forceinline__ float gsum1(Grp& G, float v) {
+    float a[1] = {v};
+    gsum<1>(G, a);
+    return a[0];
+}
+__device__ __forceinline__ ff gsum_ff(Grp& G, ff v) {
+    v = group_sum_ff<32>(v);
+    if (G.gw == 1) return v;
+    float* s = G.red + G.flip * 64;
+    if ((threadIdx.x & 31) == 0) {
+        s[G.wig * 4] = v.hi;
+        s[G.wig * 4 + 1] = v.lo;
+    }
+    grp_bar(G);
+    ff t{s[0], s[1]};
+    for (int w = 1; w < G.gw; ++w) t = ff_add(t, ff{s[w * 4], s[w * 4 + 1]});
+    G.flip ^= 1;
+    return t;
+}
+
+// ---------------------------------------------------------------- maps on a group
+// App. E, Eq. "O update" (Z ~ N(0, I/d) per coordinate; c2s = c2 / sqrt(d))
+template <int CPL>
+__device__ __forceinline__ void g_o(const KParams& P, Grp& G, uint32_t m, uint32_t t, uint32_t tag,
+                                    float c1, float c2s, float (&u)[CPL]) {
+    float n2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = G.gl + G.lpc * k;
+        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[c]) : 0.0f;
+            u[4 * k + c] = v;
+            n2 = fmaf(v, v, n2);
+        }
+    }
+    n2 = gsum1(G, n2);
+    const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) u[q] *= inv;
+}
+
+// App. E, Eq. "B MCHMC", overflow-free form (zeta = e^-delta)
+template <int CPL>
+__device__ __forceinline__ void g_b(Grp& G, float beps, float inv_dm1, float dm1, const float (&g)[CPL],
+                                    float (&u)[CPL], ff& dl) {
+    float s[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        s[0] = fmaf(g[q], g[q], s[0]);
+        s[1] = fmaf(g[q], u[q], s[1]);
+    }
+    gsum<2>(G, s);
+    const float gg = s[0], gu = s[1];
+    if (gg > 0.0f) {
+        const float gn = sqrtf(gg);
+        const float eu = gu / gn;
+        const float delta = beps * gn * inv_dm1;
+        const float zeta = expf(-delta);
+        const float om = -expm1f(-delta);
+        const float opz = 1.0f + zeta;
+        const float den = fmaf(eu, om * opz, fmaf(zeta, zeta, 1.0f));
+        const float inv = 1.0f / den;
+        const float cu = 2.0f * zeta * inv;
+        const float ce = om * fmaf(eu, om, opz) * inv / gn;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) u[q] = fmaf(cu, u[q], ce * g[q]);
+        dl = ff_add(dl, dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu))));
+    }
+}
+
+// Gaussian A map: y <- y + ae u, g at the new point, and log p(x') - log p(x)
+// in difference form -1/2 prec (x' - x)(x' + x)
+template <int CPL>
+__device__ __forceinline__ ff g_a(Grp& G, const KParams& P, float ae, float (&y)[CPL], const float (&u)[CPL],
+                                  float (&g)[CPL], const float* s_pr, const float* s_sg) {
+    float part = 0.0f;
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = G.gl + G.lpc * k;
+        if (j >= P.nblk) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int q = 4 * k + c;
+            const float pr = s_pr[4 * j + c], sg = s_sg[4 * j + c];
+            const float xo = sg * y[q];
+            const float yn = fmaf(ae, u[q], y[q]);
+            const float xn = sg * yn;
+            part = fmaf(-0.5f * pr * (xn - xo), xo + xn, part);
+            y[q] = yn;
+            g[q] = sg * (-pr * xn);
+        }
+    }
+    return gsum_ff(G, ff_make(part));
+}
+
+template <int CPL>
+__device__ __forceinline__ void g_grad(Grp& G, const KParams& P, const float (&y)[CPL], float (&g)[CPL],
+                                       const float* s_pr, const float* s_sg) {
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = G.gl + G.lpc * k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int q = 4 * k + c;
+            g[q] = 0.0f;
+            if (j < P.nblk) {
+                const float sg = s_sg[4 * j + c];
+                g[q] = sg * (-s_pr[4 * j + c] * (sg * y[q]));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int CPL>
+__global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
+    constexpr int NB = CPL / 4;
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ KParams sP;
+    __shared__ Hyper sH;
+    __shared__ Coefs CF;
+    __shared__ FinShared FS;
+    __shared__ float s_eps, s_c1, s_c2s;
+    __shared__ int s_live;
+    float* qbuf = reinterpret_cast<float*>(bsm);   // [2][ng][lpc CPL]: per-thread column sums
+    float* s_pr = qbuf + 2 * kBT * CPL;            // [cap_pad] precisions
+    float* s_sg = s_pr + B.cap_pad;                // [cap_pad] preconditioner
+    float* s_red = s_sg + B.cap_pad;               // [kBW][kRed]
+    ff* s_cs = reinterpret_cast<ff*>(s_red + kBW * kRed);  // [kBW][NCS]
+    ff* s_q = s_cs + kBW * NCS;                    // [NQ SL + NCS]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    for (int i = tid; i < (int)(sizeof(Coefs) / 4); i += kBT)
+        reinterpret_cast<int*>(&CF)[i] = reinterpret_cast<const int*>(B.coefs)[i];
+
+    // the problem's parameters and phase machine into shared memory
+    auto load_prob = [&](int p) {
+        __syncthreads();
+        const int* src = reinterpret_cast<const int*>(B.probs + p);
+        for (int i = tid; i < (int)(sizeof(KParams) / 4); i += kBT) reinterpret_cast<int*>(&sP)[i] = src[i];
+        __syncthreads();
+        if (tid == 0) {
+            sP.mode = B.mode;
+            sP.G = G;
+            sH = *sP.hyper;
+            set_step_scalars(sH, sP.d, s_eps, s_c1, s_c2s);
+        }
+        __syncthreads();
+    };
+
+    unsigned n_bar = 0;
+    const int n_iter = B.mode == 0 ? 1 : B.n_iters;
+    for (int it = 0; it < n_iter; ++it) {
+        if (tid == 0) {
+            int live = 0;
+            for (int p = 0; p < B.n; ++p) live |= (B.mode == 0 || !B.probs[p].hyper->done) ? 1 : 0;
+            s_live = live;
+        }
+        __syncthreads();
+        if (!s_live) break;  // uniform: every block reads the same phase machines
+        // ------------------------------------------------ 1. chain phase
+        for (int p = 0; p < B.n; ++p) {
+            load_prob(p);
+            if (B.mode == 1 && sH.done) continue;
+            const KParams& P = sP;
+            for (int i = tid; i < P.d_pad; i += kBT) {
+                s_pr[i] = i < P.d ? P.prec[i] : 0.0f;
+                s_sg[i] = P.sigma[i];
+            }
+            const int gw = B.gw[p], ng = kBW / gw;
+            Grp Gc{gw, warp / gw, warp % gw, (warp % gw) * 32 + lane, 32 * gw, s_red + (warp / gw) * kRed, 0};
+            const int cap = Gc.lpc * CPL;
+            float* q0 = qbuf + (size_t)(0 * ng + Gc.grp) * cap;
+            float* q1 = qbuf + (size_t)(1 * ng + Gc.grp) * cap;
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = 4 * (Gc.gl + Gc.lpc * k) + c;
+                    q0[i] = 0.0f;
+                    q1[i] = 0.0f;
+                }
+            ff cs[NCS];
+#pragma unroll
+            for (int k = 0; k < NCS; ++k) cs[k] = ff_make(0.0f);
+            __syncthreads();
+            const float eps = s_eps, c1 = s_c1, c2s = s_c2s;
+            const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
+            const bool pend = (B.mode == 1 && sH.phase == 1 && sH.p == 0);  // y still in x (switch)
+            const int64_t m0 = (int64_t)b * P.M / G, m1 = (int64_t)(b + 1) * P.M / G;
+            for (int64_t mm = m0 + Gc.grp; mm < m1; mm += ng) {
+                const uint32_t m = (uint32_t)mm;
+                float y[CPL], u[CPL], g[CPL];
+                auto load = [&](const float* src, float(&v)[CPL]) {
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const int j = Gc.gl + Gc.lpc * k;
+                        float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (j < P.nblk) a = *reinterpret_cast<const float4*>(src + (size_t)mm * P.d_pad + 4 * j);
+                        v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+                    }
+                };
+                auto store = [&](float* dst, const float(&v)[CPL]) {
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const int j = Gc.gl + Gc.lpc * k;
+                        if (j < P.nblk)
+                            *reinterpret_cast<float4*>(dst + (size_t)mm * P.d_pad + 4 * j) =
+                                make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    }
+                };
+                if (B.mode == 0) {
+                    // Alg. 1 input and App. C "Initialization"
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const int j = Gc.gl + Gc.lpc * k;
+                        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        if (j < P.nblk && P.x0 == nullptr)
+                            normals4(j, m, 0u, TAG_X0 | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int i = 4 * j + c;
+                            y[4 * k + c] = (j < P.nblk && i < P.d)
+                                               ? (P.x0 ? P.x0[(size_t)mm * P.d + i] : P.x0_scale * z[c])
+                                               : 0.0f;
+                        }
+                    }
+                    g_grad<CPL>(Gc, P, y, g, s_pr, s_sg);
+                    float n2 = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) n2 = fmaf(g[q], g[q], n2);
+                    n2 = gsum1(Gc, n2);
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) u[q] = 0.0f;
+                    g_o<CPL>(P, Gc, m, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
+                    if (n2 > 0.0f) {
+                        const float inv = 1.0f / sqrtf(n2);
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) u[q] = g[q] * inv;
+                    }
+                    bool bad = false;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) bad = bad || !(isfinite(y[q]) && isfinite(g[q]));
+                    if (bad) atomicCAS(P.status, ST_OK, ST_NONFINITE);
+                    store(P.y, y);
+                    store(P.u, u);
+                } else {
+                    load(P.y, y);
+                    load(P.u, u);
+                    if (pend)  // Sec. 4: the preconditioner fixed at the switch, y = x / sigma
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) {
+                            const int j = Gc.gl + Gc.lpc * k;
+                            if (j < P.nblk)
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) y[4 * k + c] = y[4 * k + c] / s_sg[4 * j + c];
+                        }
+                    g_grad<CPL>(Gc, P, y, g, s_pr, s_sg);
+                    ff dl = ff_make(0.0f);
+                    const int integ = sH.phase == 0 ? INTEG_LF : sH.integ;
+                    const int K = CF.K[integ];
+                    auto phi = [&]() {
+                        for (int k = 0; k < K; ++k) {
+                            g_b<CPL>(Gc, CF.b[integ][k] * eps, inv_dm1, dm1, g, u, dl);
+                            if (k < K - 1) {
+                                const ff dlp = g_a<CPL>(Gc, P, CF.a[integ][k] * eps, y, u, g, s_pr, s_sg);
+                                dl = ff_add(dl, ff_neg(dlp));
+                            }
+                        }
+                    };
+                    if (sH.phase == 0) {
+                        const uint32_t t = (uint32_t)sH.t;
+                        g_o<CPL>(P, Gc, m, t, TAG_O1, c1, c2s, u);
+                        phi();
+                        g_o<CPL>(P, Gc, m, t, TAG_O2, c1, c2s, u);
+                    } else {
+                        // App. F step 2: u uniform on the sphere, then N steps
+                        float n2 = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) {
+                            const int j = Gc.gl + Gc.lpc * k;
+                            float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                            if (j < P.nblk)
+                                normals4(j, m, (uint32_t)sH.p, TAG_REFRESH | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float v = (4 * j + c < P.d) ? z[c] : 0.0f;
+                                u[4 * k + c] = v;
+                                n2 = fmaf(v, v, n2);
+                            }
+                        }
+                        n2 = gsum1(Gc, n2);
+                        const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) u[q] *= inv;
+                        const uint32_t t0 = (uint32_t)sH.t;
+                        for (int n = 0; n < P.N; ++n) {
+                            g_o<CPL>(P, Gc, m, t0 + n, TAG_O1, c1, c2s, u);
+                            phi();
+                            g_o<CPL>(P, Gc, m, t0 + n, TAG_O2, c1, c2s, u);
+                        }
+                    }
+                    float badf = isfinite(dl.hi) ? 0.0f : 1.0f;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        if (!(isfinite(y[q]) && isfinite(u[q]))) badf = 1.0f;
+                    const bool bad = gsum1(Gc, badf) > 0.0f;
+                    bool keep = !bad;
+                    float a_m = 0.0f;
+                    if (sH.phase == 1) {
+                        // App. F step 5: accept with probability min(1, e^-Delta)
+                        const uint4 r = philox4x32_10(
+                            make_uint4(0u, m, (uint32_t)sH.p, TAG_MH | (P.pid << 8)), P.seed_lo, P.seed_hi);
+                        const ff s = ff_add(dl, logf(u01(r.x)));
+                        keep = !bad && (s.hi < 0.0f || (s.hi == 0.0f && s.lo < 0.0f));
+                        a_m = bad ? 0.0f : (dl.hi <= 0.0f ? 1.0f : expf(-(dl.hi + dl.lo)));
+                    }
+                    if (keep) {
+                        store(P.y, y);
+                        store(P.u, u);
+                    } else {
+                        load(P.y, y);  // the accepted state stays and enters the sums
+                        if (pend)
+#pragma unroll
+                            for (int k = 0; k < NB; ++k) {
+                                const int j = Gc.gl + Gc.lpc * k;
+                                if (j < P.nblk)
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c) y[4 * k + c] = y[4 * k + c] / s_sg[4 * j + c];
+                            }
+                        if (pend) store(P.y, y);  // keep the accepted point in the new coordinates
+                    }
+                    if (sH.phase == 0) {
+                        if (bad) {
+                            cs[CS_NBAD] = ff_add(cs[CS_NBAD], 1.0f);
+                        } else {
+                            cs[CS_DSUM] = ff_add(cs[CS_DSUM], dl);
+                            cs[CS_DSQ] = ff_add(cs[CS_DSQ], ff_f(dl) * ff_f(dl));
+                            cs[CS_NFIN] = ff_add(cs[CS_NFIN], 1.0f);
+                        }
+                    } else {
+                        cs[CS_ASUM] = ff_add(cs[CS_ASUM], a_m);
+                        if (bad) cs[CS_NBAD] = ff_add(cs[CS_NBAD], 1.0f);
+                    }
+                }
+                // per-coordinate sums of y and y^2 (this thread's own slots)
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int i = 4 * (Gc.gl + Gc.lpc * k) + c;
+                        const float v = y[4 * k + c];
+                        q0[i] += v;
+                        q1[i] = fmaf(v, v, q1[i]);
+                    }
+            }
+            if (lane == 0 && Gc.wig == 0)
+#pragma unroll
+                for (int k = 0; k < NCS; ++k) s_cs[Gc.grp * NCS + k] = cs[k];
+            __syncthreads();
+            // this block's column of the problem: groups in order, float-float
+            const int G2 = P.G, dp = P.d_pad;
+            for (int i = tid; i < P.d; i += kBT)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float* src = qbuf + (size_t)q * ng * cap + i;
+                    ff s = ff_make(src[0]);
+                    for (int gg = 1; gg < ng; ++gg) s = ff_add(s, src[(size_t)gg * cap]);
+                    P.part[((size_t)q * dp + i) * G2 + b] = make_float2(s.hi, s.lo);
+                }
+            if (tid < NCS) {
+                ff s = s_cs[tid];
+                for (int gg = 1; gg < ng; ++gg) s = ff_add(s, s_cs[gg * NCS + tid]);
+                P.part[((size_t)NQ * dp + tid) * G2 + b] = make_float2(s.hi, s.lo);
+            }
+        }
+        // ------------------------------------------------ 2. slices
+        n_bar += 1;
+        if (!grid_sync_count(B.bar_count, B.status, n_bar * (unsigned)(G + B.bar_extra), B.timeout_ns)) return;
+        {
+            int task = 0;
+            for (int p = 0; p < B.n; ++p) {
+                const int d = B.probs[p].d;
+                const int nsl = (d + B.SL - 1) / B.SL;
+                for (int s = 0; s < nsl; ++s, ++task) {
+                    if (task % G != b) continue;
+                    load_prob(p);
+                    if (B.mode == 1 && sH.done) continue;
+                    ens_slice(sP, sH, s_q, s, nsl);
+                }
+            }
+        }
+        // ------------------------------------------------ 3. finalise per problem
+        n_bar += 1;
+        if (!grid_sync_count(B.bar_count, B.status, n_bar * (unsigned)(G + B.bar_extra), B.timeout_ns)) return;
+        for (int p = b; p < B.n; p += G) {
+            load_prob(p);
+            if (B.mode == 1 && sH.done) continue;
+            ens_gather(sP, sH, qbuf, FS);
+            if (tid == 0) {
+                *sP.hyper = sH;
+                ens_trace_row(sP, sH, FS.now);
+            }
+            if (FS.sw)  // Sec. 4: the diagonal preconditioner, applied to y at the next load
+                for (int i = tid; i < sP.d; i += kBT) {
+                    const float v = qbuf[i];
+                    sP.sigma[i] = v > 0.0f ? sqrtf(v) : 1.0f;
+                }
+        }
+        n_bar += 1;
+        if (!grid_sync_count(B.bar_count, B.status, n_bar * (unsigned)(G + B.bar_extra), B.timeout_ns)) return;
+    }
+}
+
+// ---------------------------------------------------------------- host
+const void* batch_fn(int cpl) {
+    switch (cpl) {
+    case 8: return (const void*)batch_kernel<8>;
+    case 12: return (const void*)batch_kernel<12>;
+    case 16: return (const void*)batch_kernel<16>;
+    case 20: return (const void*)batch_kernel<20>;
+    }
+    return nullptr;
+}
+
+size_t batch_smem(int cpl, int cap_pad, int SL) {
+    return (size_t)2 * kBT * cpl * 4 + (size_t)2 * cap_pad * 4 + (size_t)kBW * kRed * 4 +
+           (size_t)kBW * NCS * sizeof(ff) + ((size_t)NQ * SL + NCS) * sizeof(ff);
+}
+
+int batch_threads() { return kBT; }
+
+// warps per chain for dimension d with cpl coordinates per lane; 0 if it does not fit
+int batch_gw(int64_t d, int cpl, int widen) {
+    int gw = 1;
+    while ((int64_t)32 * gw * cpl < ((d + 3) / 4) * 4 && gw < kBW) gw *= 2;
+    if ((int64_t)32 * gw * cpl < ((d + 3) / 4) * 4) return 0;
+    for (int k = 0; k < widen && gw < kBW; ++k) gw *= 2;
+    return gw;
+}
+
+cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const Coefs* coefs, int n,
+                         int mode, int n_iters, int SL, int cap_pad, unsigned* bar, int* status,
+                         long long timeout_ns, int bar_extra, cudaStream_t st) {
+    BatchArgs a;
+    a.probs = probs;
+    a.gw = gw;
+    a.coefs = coefs;
+    a.n = n;
+    a.mode = mode;
+    a.n_iters = n_iters;
+    a.SL = SL;
+    a.cap_pad = cap_pad;
+    a.bar_count = bar;
+    a.status = status;
+    a.timeout_ns = timeout_ns;
+    a.bar_extra = bar_extra;
+    const void* fn = batch_fn(cpl);
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = batch_smem(cpl, cap_pad, SL);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int batch_blocks_per_sm(int cpl, int cap_pad, int SL) {
+    const void* fn = batch_fn(cpl);
+    const size_t smem = batch_smem(cpl, cap_pad, SL);
+    if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBT, smem) != cudaSuccess) return 0;
+    return bps;
+}
+
+}  // namespace laps

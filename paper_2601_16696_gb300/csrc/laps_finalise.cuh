@@ -32,9 +32,10 @@ struct FinShared {
     unsigned long long now;           // %globaltimer at the finalise
 };
 
-// quantities per coordinate reduced this iteration (the g sums are unused after the switch)
+// quantities per coordinate reduced this iteration (the g sums are unused after the
+// switch; a diagonal Gaussian derives them from the y sums)
 __device__ __forceinline__ int ens_nq(const KParams& P, const Hyper& H) {
-    return (H.phase == 1 && P.mode == 1) ? 2 : NQ;
+    return (P.gauss_derived || (H.phase == 1 && P.mode == 1)) ? 2 : NQ;
 }
 
 // Step 3.  s_q: shared [NQ][P.smax] + [NCS] float-float.  All threads of the block call it.
@@ -91,6 +92,10 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
             const ff eg = ff_mulf(s_q[2 * P.smax + k], iM);
             const ff eyg = ff_mulf(s_q[3 * P.smax + k], iM);
             const float V = -ff_f(ff_add(eyg, ff_neg(ff_mul(mean, eg))));
+            dv = (1.0f - V) * (1.0f - V);
+        } else if (P.gauss_derived && (P.mode == 0 || H.phase == 0)) {
+            // diagonal Gaussian: g_i = -prec_i sigma_i^2 y_i, so V_ii = prec_i sigma_i^2 Var[y_i]
+            const float V = P.prec[i] * s2i * var_y;
             dv = (1.0f - V) * (1.0f - V);
         }
         if (push) {

@@ -74,6 +74,16 @@ laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t
 laps_status launch_resident(laps_ctx* c, int mode, int n_iters, const float* x0, float x0_scale,
                             cudaStream_t st);
 void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, KParams& P);
+Hyper initial_hyper();
+// batched problems (laps_batch.cu)
+const void* batch_fn(int cpl);
+size_t batch_smem(int cpl, int cap_pad, int SL);
+int batch_threads();
+int batch_gw(int64_t d, int cpl, int widen);
+int batch_blocks_per_sm(int cpl, int cap_pad, int SL);
+cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const Coefs* coefs, int n,
+                         int mode, int n_iters, int SL, int cap_pad, unsigned* bar, int* status,
+                         long long timeout_ns, int bar_extra, cudaStream_t st);
 // streamed path (laps_streamed.cu)
 laps_status streamed_setup(laps_ctx* c);
 laps_status streamed_alloc(laps_ctx* c);

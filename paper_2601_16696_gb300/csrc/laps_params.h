@@ -83,6 +83,7 @@ struct KParams {
     int nsplit;               // S
     int* go;                  // [2]: the iteration is live; it switched to the adjusted phase
     void* Wb;                 // mixed precision: [M_pad][2 d_pad] BF16 (hi | lo) copy of W
+    int gauss_derived;        // batched diagonal Gaussians: only y, y^2 are summed per coordinate
 };
 
 // one launch of the streamed path's chain-update kernel: the maps it applies,

@@ -11,6 +11,8 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +71,16 @@ class TraceRow(C.Structure):
                 ("time_ns", C.c_double)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("d", C.c_int64), ("M", C.c_int64), ("prec", C.c_void_p), ("x0", C.c_void_p),
+                ("x0_scale", C.c_double)]
+
+
+class BatchShape(C.Structure):
+    _fields_ = [("coords_per_lane", C.c_int), ("widen", C.c_int), ("slice", C.c_int),
+                ("threads", C.c_int), ("blocks", C.c_int), ("tuned", C.c_int)]
+
+
 class LaunchInfo(C.Structure):
     _fields_ = [("chains_per_block", C.c_int), ("lanes_per_chain", C.c_int),
                 ("coords_per_lane", C.c_int), ("threads", C.c_int), ("blocks", C.c_int),
@@ -110,6 +122,21 @@ SIGNATURES = {
     "laps_get_launch_info": (C.c_int, [_vp, C.POINTER(LaunchInfo)]),
     "laps_run_noalloc": (C.c_int, [C.POINTER(TargetDesc), C.c_int64, C.POINTER(Config), _vp,
                                    C.c_double, C.c_uint64, _vp, C.POINTER(Stats), _vp]),
+    "laps_batch_create": (C.c_int, [C.POINTER(Problem), C.c_int, C.POINTER(Config),
+                                    C.POINTER(_vp)]),
+    "laps_batch_destroy": (None, [_vp]),
+    "laps_batch_set_truth": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
+    "laps_batch_init": (C.c_int, [_vp, C.c_uint64, _vp]),
+    "laps_batch_step": (C.c_int, [_vp, C.c_int, _vp]),
+    "laps_batch_run": (C.c_int, [_vp, C.c_int, _vp]),
+    "laps_batch_tune": (C.c_int, [_vp, _vp]),
+    "laps_batch_get_shape": (C.c_int, [_vp, C.POINTER(BatchShape)]),
+    "laps_batch_set_shape": (C.c_int, [_vp, C.POINTER(BatchShape)]),
+    "laps_batch_get_stats": (C.c_int, [_vp, C.c_int, C.POINTER(Stats)]),
+    "laps_batch_get_trace": (C.c_int, [_vp, C.c_int, C.POINTER(TraceRow), C.c_int,
+                                       C.POINTER(C.c_int)]),
+    "laps_batch_sample": (C.c_int, [_vp, C.c_int, _vp, _vp]),
 }
 
 
@@ -325,3 +352,79 @@ def run_noalloc(kind: int, d: int, M: int, x0: torch.Tensor | None, seed: int,
     _check(lib().laps_run_noalloc(C.byref(desc), M, C.byref(cfg), _ptr(x0), x0_scale, seed,
                                   _ptr(out), C.byref(s), _stream(stream)))
     return _as_dict(s)
+
+
+class Batch:
+    """Independent diagonal-Gaussian problems in one persistent launch
+    (laps_batch_*).  ``problems``: objects with d, M, prec (and optionally x0)."""
+
+    def __init__(self, problems, config: Config | None = None, x0_scale: float = 1.0,
+                 use_x0: bool = True, **cfg_kw):
+        self.config = config if config is not None else default_config(**cfg_kw)
+        self.n = len(problems)
+        self.dims = [(int(p.d), int(p.M)) for p in problems]
+        self._keep = []
+        arr = (Problem * self.n)()
+        for k, p in enumerate(problems):
+            pr = torch.as_tensor(p.prec, dtype=torch.float32, device="cuda").contiguous()
+            self._keep.append(pr)
+            x0 = None
+            if use_x0 and getattr(p, "x0", None) is not None:
+                x0 = torch.as_tensor(p.x0, dtype=torch.float32, device="cuda").contiguous()
+                self._keep.append(x0)
+            arr[k] = Problem(p.d, p.M, pr.data_ptr(), x0.data_ptr() if x0 is not None else None,
+                             x0_scale)
+        h = C.c_void_p()
+        _check(lib().laps_batch_create(arr, self.n, C.byref(self.config), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.laps_batch_destroy(h)
+            self._h = None
+
+    def set_truth(self, k: int, Ex2, Varx2):
+        a = np.ascontiguousarray(Ex2, dtype=np.float64)
+        b = np.ascontiguousarray(Varx2, dtype=np.float64)
+        _check(lib().laps_batch_set_truth(self._h, k, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                          b.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def init(self, seed: int = 0, stream=None):
+        _check(lib().laps_batch_init(self._h, seed, _stream(stream)))
+
+    def step(self, n: int = 1, stream=None):
+        _check(lib().laps_batch_step(self._h, n, _stream(stream)))
+
+    def run(self, iters_per_launch: int = 64, stream=None):
+        _check(lib().laps_batch_run(self._h, iters_per_launch, _stream(stream)))
+
+    def tune(self, stream=None):
+        _check(lib().laps_batch_tune(self._h, _stream(stream)))
+
+    def shape(self) -> dict:
+        s = BatchShape()
+        _check(lib().laps_batch_get_shape(self._h, C.byref(s)))
+        return _as_dict(s)
+
+    def set_shape(self, coords_per_lane: int, widen: int = 0, slice: int = 64):
+        s = BatchShape(coords_per_lane, widen, slice, 0, 0, 0)
+        _check(lib().laps_batch_set_shape(self._h, C.byref(s)))
+
+    def stats(self, k: int) -> dict:
+        s = Stats()
+        _check(lib().laps_batch_get_stats(self._h, k, C.byref(s)))
+        return _as_dict(s)
+
+    def trace(self, k: int) -> list:
+        n = C.c_int(0)
+        _check(lib().laps_batch_get_trace(self._h, k, None, 0, C.byref(n)))
+        rows = (TraceRow * max(1, n.value))()
+        _check(lib().laps_batch_get_trace(self._h, k, rows, n.value, C.byref(n)))
+        return [_as_dict(rows[i]) for i in range(n.value)]
+
+    def sample(self, k: int, stream=None) -> torch.Tensor:
+        d, M = self.dims[k]
+        out = torch.empty(M, d, dtype=torch.float32, device="cuda")
+        _check(lib().laps_batch_sample(self._h, k, _ptr(out), _stream(stream)))
+        return out
