@@ -164,6 +164,111 @@ def run_reference(args):
     return 0
 
 
+def _peaks():
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return json.load(f)
+
+
+def _forms(flush, stream, mhz, seed0):
+    """The other forms of the path, measured in the same run and reported
+    beside the headline: the logistic regression (d = 101 with intercept,
+    n = 10^4 rows, M = 8192) with the BF16 tensor-core contraction in the
+    unadjusted phase beside the all-FP32 form, and the batch of 64 uneven
+    diagonal Gaussians plus one d = 10^4, M = 16384 problem in one persistent
+    launch.  Each: chain-gradient evaluations per second of a whole run, wall
+    time to b^2 < 0.01, and the dominant kernel against its roofline."""
+    import torch
+    from paper_2601_16696_gb300 import laps, workloads
+    pk = _peaks()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * mhz * 1e6 / 1e12  # TFLOP/s, FMA lanes x 2 x clock
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed_ms(fn):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    out = {}
+    # ---- logistic regression
+    pr = workloads.logreg(with_truth=True)
+    tg = laps.Target.from_problem(pr)
+    x0 = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
+    n = pr.X.shape[0]
+    flops = 4.0 * pr.M * n * pr.d  # Z = W X^T and G = R X per gradient of the ensemble
+    lr = {"workload": "logreg_d%d_n%d_M%d_%dsteps" % (pr.d, n, pr.M, pr.n_steps),
+          "b2": "b2_max", "truth": "Laplace approximation of the posterior (FP64)",
+          "switch": "paper rule (max delta < 0.01)"}
+    for name, prec in (("mixed", 1), ("fp32", 0)):
+        for _ in range(3):
+            tg.logp_grad(x0, precision=prec)
+        reps = 10
+        gms = timed_ms(lambda: [tg.logp_grad(x0, precision=prec) for _ in range(reps)]) / reps
+        tg.check()
+        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, precision=prec, stop_b2=0.01,
+                         stop_b2_max=1)
+        s.set_truth(pr.Ex2, pr.Varx2)
+        s.init(x0, seed=seed0)
+        s.step(3)  # warm-up of the launch sequence
+        run_ms = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
+        st = s.stats()
+        achieved = flops / (gms * 1e-3) / 1e12
+        peak = pk["bf16_tflops"] if prec == 1 else fp32_peak
+        lr[name] = {
+            "value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT,
+            "run_ms": run_ms, "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
+            "time_to_b2_ms": st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None,
+            "b2_max_final": st["b2_max"],
+            "roofline": {"bound": "tensor" if prec == 1 else "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "kernel": "logreg_grad_mma_kernel<128>" if prec == 1
+                         else "logreg_grad_f32_kernel<128>",
+                         "timed": "laps_target_logp_grad_prec (points packed, contraction, "
+                                  "partials summed), %.3f ms per call" % gms,
+                         "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)" if prec == 1
+                         else "%d SMs x 128 FP32 FMA lanes x 2 x %.0f MHz" % (nsm, mhz)}}
+    out["logreg"] = lr
+    # ---- the batch
+    probs = workloads.batch64()
+    coords = sum(p.d * p.M for p in probs)
+    b = laps.Batch(probs, use_x0=False, n_total_steps=2000)
+    for k, p in enumerate(probs):
+        b.set_truth(k, p.Ex2, p.Varx2)
+    b.init(seed=seed0)
+    b.tune()
+    b.step(2)
+    it_ms = timed_ms(lambda: b.step(5)) / 5  # unadjusted iterations of every problem
+    b.init(seed=seed0 + 1)
+    run_ms = timed_ms(lambda: b.run(iters_per_launch=64))
+    sts = [b.stats(k) for k in range(len(probs))]
+    grads = sum(p.M * s["grads"] for p, s in zip(probs, sts))
+    firsts = [s["b2_first_ns"] / 1e6 for s in sts if s["b2_first_t"] >= 0]
+    achieved = coords * 16 / (it_ms * 1e-3) / 1e9
+    out["batch"] = {
+        "workload": "batch64: 64 Gaussians d in [10, 2000], M in {512..4096}, "
+                    "+ d=10000 M=16384; 2000 steps, paper switch rule",
+        "problems": len(probs), "coordinates": coords,
+        "value": grads / (run_ms * 1e-3), "unit": UNIT, "run_ms": run_ms,
+        "time_to_b2_ms": {"b2": "b2_avg", "reached": len(firsts), "of": len(probs),
+                          "max": max(firsts) if firsts else None,
+                          "median": statistics.median(firsts) if firsts else None},
+        "shape": b.shape(),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "batch_kernel<%d>" % b.shape()["coords_per_lane"],
+                     "basis": "16 B per coordinate-step (y, u read and written), %.3f ms per "
+                              "unadjusted iteration of the whole batch" % it_ms},
+    }
+    return out
+
+
 def ncu_case():
     import torch
     from paper_2601_16696_gb300 import build, laps, workloads
@@ -186,6 +291,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="laps", choices=["laps", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the logistic-regression and batch forms")
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the workload's launch shape, one launch of 200 unadjusted "
                          "iterations after two others (the case profiled under ncu)")
@@ -332,6 +439,8 @@ def main():
             "time_to_b2": time_to_b2, "roofline": roofline, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clocks,
         }
+        if not args.no_forms:
+            line["forms"] = _forms(flush, stream, mhz, seed_base + 500)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(pr)
         print(json.dumps(line))

@@ -154,6 +154,16 @@ void laps_target_destroy(laps_target* tg);
  * kernels the sampler uses), FP32 in and out with compensated sums. */
 laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
                                   float* logp, float* grad, void* stream);
+/* The same in a given arithmetic: LAPS_FP32 is laps_target_logp_grad;
+ * LAPS_MIXED (LOGREG with d <= 128) is the tensor-core form the sampler's
+ * unadjusted phase uses: the target on the BF16-rounded data, each point as a
+ * sum of two BF16 terms, residuals y - sigmoid(z) in BF16, FP32 accumulation.
+ * Stream-ordered; a bounded device wait that expired is latched in the
+ * target's status word, which laps_target_status returns. */
+laps_status laps_target_logp_grad_prec(const laps_target* tg, const float* x, int64_t M,
+                                       float* logp, float* grad, int precision, void* stream);
+/* Synchronises the device, returns and clears the target's latched status. */
+laps_status laps_target_status(laps_target* tg);
 
 /* ---- one sampling problem ---------------------------------------------- */
 /* Allocates the ensemble state (x, u, g, log p in the sampler's layout), the

@@ -371,6 +371,11 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
             if (L.Xtb) cudaFree(L.Xtb);
             L.Xb = L.Xtb = nullptr;
         }
+        if (cudaMalloc(&t->status, sizeof(int)) != cudaSuccess ||
+            cudaMemset(t->status, 0, sizeof(int)) != cudaSuccess) {
+            laps_target_destroy(t);
+            return fail(LAPS_ERR_OOM, "LOGREG status word");
+        }
     }
     *out = t;
     return LAPS_OK;
@@ -383,6 +388,7 @@ void laps_target_destroy(laps_target* t) {
     if (t->lr.y) cudaFree(t->lr.y);
     if (t->lr.Xb) cudaFree(t->lr.Xb);
     if (t->lr.Xtb) cudaFree(t->lr.Xtb);
+    if (t->status) cudaFree(t->status);
     delete t;
 }
 

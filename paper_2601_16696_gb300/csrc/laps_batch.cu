@@ -136,15 +136,39 @@ __device__ __forceinline__ void g_o(const KParams& P, Grp& G, uint32_t m, uint32
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
 
+// The gradient in y of the diagonal Gaussian, g_y = sigma o (-prec o (sigma o y)),
+// for this thread's coordinate block k (recomputed where needed: it is three
+// multiplies, cheaper than keeping it in registers)
+template <int CPL>
+__device__ __forceinline__ void g_blk(const Grp& G, const KParams& P, const float (&y)[CPL], int k,
+                                      const float4* s_pr4, const float4* s_sg4, float (&g)[4]) {
+    const int j = G.gl + G.lpc * k;
+    if (j >= P.nblk) {
+        g[0] = g[1] = g[2] = g[3] = 0.0f;
+        return;
+    }
+    const float4 pr = s_pr4[j], sg = s_sg4[j];
+    g[0] = sg.x * (-pr.x * (sg.x * y[4 * k]));
+    g[1] = sg.y * (-pr.y * (sg.y * y[4 * k + 1]));
+    g[2] = sg.z * (-pr.z * (sg.z * y[4 * k + 2]));
+    g[3] = sg.w * (-pr.w * (sg.w * y[4 * k + 3]));
+}
+
 // App. E, Eq. "B MCHMC", overflow-free form (zeta = e^-delta)
 template <int CPL>
-__device__ __forceinline__ void g_b(Grp& G, float beps, float inv_dm1, float dm1, const float (&g)[CPL],
-                                    float (&u)[CPL], ff& dl) {
+__device__ __forceinline__ void g_b(Grp& G, const KParams& P, float beps, float inv_dm1, float dm1,
+                                    const float (&y)[CPL], float (&u)[CPL], ff& dl, const float4* s_pr4,
+                                    const float4* s_sg4) {
     float s[2] = {0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-        s[0] = fmaf(g[q], g[q], s[0]);
-        s[1] = fmaf(g[q], u[q], s[1]);
+    for (int k = 0; k < CPL / 4; ++k) {
+        float g[4];
+        g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            s[0] = fmaf(g[c], g[c], s[0]);
+            s[1] = fmaf(g[c], u[4 * k + c], s[1]);
+        }
     }
     gsum<2>(G, s);
     const float gg = s[0], gu = s[1];
@@ -160,52 +184,40 @@ __device__ __forceinline__ void g_b(Grp& G, float beps, float inv_dm1, float dm1
         const float cu = 2.0f * zeta * inv;
         const float ce = om * fmaf(eu, om, opz) * inv / gn;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) u[q] = fmaf(cu, u[q], ce * g[q]);
+        for (int k = 0; k < CPL / 4; ++k) {
+            float g[4];
+            g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) u[4 * k + c] = fmaf(cu, u[4 * k + c], ce * g[c]);
+        }
         dl = ff_add(dl, dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu))));
     }
 }
 
-// Gaussian A map: y <- y + ae u, g at the new point, and log p(x') - log p(x)
-// in difference form -1/2 prec (x' - x)(x' + x)
+// Gaussian A map: y <- y + ae u and log p(x') - log p(x) in difference form
+// -1/2 prec (x' - x)(x' + x)
 template <int CPL>
 __device__ __forceinline__ ff g_a(Grp& G, const KParams& P, float ae, float (&y)[CPL], const float (&u)[CPL],
-                                  float (&g)[CPL], const float* s_pr, const float* s_sg) {
+                                  const float4* s_pr4, const float4* s_sg4) {
     float part = 0.0f;
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         const int j = G.gl + G.lpc * k;
         if (j >= P.nblk) continue;
+        const float4 pr4 = s_pr4[j], sg4 = s_sg4[j];
+        const float prs[4] = {pr4.x, pr4.y, pr4.z, pr4.w}, sgs[4] = {sg4.x, sg4.y, sg4.z, sg4.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int q = 4 * k + c;
-            const float pr = s_pr[4 * j + c], sg = s_sg[4 * j + c];
+            const float pr = prs[c], sg = sgs[c];
             const float xo = sg * y[q];
             const float yn = fmaf(ae, u[q], y[q]);
             const float xn = sg * yn;
             part = fmaf(-0.5f * pr * (xn - xo), xo + xn, part);
             y[q] = yn;
-            g[q] = sg * (-pr * xn);
         }
     }
     return gsum_ff(G, ff_make(part));
-}
-
-template <int CPL>
-__device__ __forceinline__ void g_grad(Grp& G, const KParams& P, const float (&y)[CPL], float (&g)[CPL],
-                                       const float* s_pr, const float* s_sg) {
-#pragma unroll
-    for (int k = 0; k < CPL / 4; ++k) {
-        const int j = G.gl + G.lpc * k;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int q = 4 * k + c;
-            g[q] = 0.0f;
-            if (j < P.nblk) {
-                const float sg = s_sg[4 * j + c];
-                g[q] = sg * (-s_pr[4 * j + c] * (sg * y[q]));
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -268,16 +280,17 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
             const int gw = B.gw[p], ng = kBW / gw;
             Grp Gc{gw, warp / gw, warp % gw, (warp % gw) * 32 + lane, 32 * gw, s_red + (warp / gw) * kRed, 0};
             const int cap = Gc.lpc * CPL;
-            float* q0 = qbuf + (size_t)(0 * ng + Gc.grp) * cap;
-            float* q1 = qbuf + (size_t)(1 * ng + Gc.grp) * cap;
+            // this thread's column slots, one float4 per coordinate block (conflict-free)
+            float4* q0 = reinterpret_cast<float4*>(qbuf + (size_t)(0 * ng + Gc.grp) * cap);
+            float4* q1 = reinterpret_cast<float4*>(qbuf + (size_t)(1 * ng + Gc.grp) * cap);
+            const float4* s_pr4 = reinterpret_cast<const float4*>(s_pr);
+            const float4* s_sg4 = reinterpret_cast<const float4*>(s_sg);
 #pragma unroll
-            for (int k = 0; k < NB; ++k)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int i = 4 * (Gc.gl + Gc.lpc * k) + c;
-                    q0[i] = 0.0f;
-                    q1[i] = 0.0f;
-                }
+            for (int k = 0; k < NB; ++k) {
+                const int j = Gc.gl + Gc.lpc * k;
+                q0[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                q1[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
             ff cs[NCS];
 #pragma unroll
             for (int k = 0; k < NCS; ++k) cs[k] = ff_make(0.0f);
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
             const int64_t m0 = (int64_t)b * P.M / G, m1 = (int64_t)(b + 1) * P.M / G;
             for (int64_t mm = m0 + Gc.grp; mm < m1; mm += ng) {
                 const uint32_t m = (uint32_t)mm;
-                float y[CPL], u[CPL], g[CPL];
+                float y[CPL], u[CPL];
                 auto load = [&](const float* src, float(&v)[CPL]) {
 #pragma unroll
                     for (int k = 0; k < NB; ++k) {
@@ -323,10 +336,18 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                                                : 0.0f;
                         }
                     }
-                    g_grad<CPL>(Gc, P, y, g, s_pr, s_sg);
                     float n2 = 0.0f;
+                    bool bad = false;
 #pragma unroll
-                    for (int q = 0; q < CPL; ++q) n2 = fmaf(g[q], g[q], n2);
+                    for (int k = 0; k < NB; ++k) {
+                        float g[4];
+                        g_blk<CPL>(Gc, P, y, k, s_pr4, s_sg4, g);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            n2 = fmaf(g[c], g[c], n2);
+                            bad = bad || !(isfinite(y[4 * k + c]) && isfinite(g[c]));
+                        }
+                    }
                     n2 = gsum1(Gc, n2);
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) u[q] = 0.0f;
@@ -334,11 +355,13 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                     if (n2 > 0.0f) {
                         const float inv = 1.0f / sqrtf(n2);
 #pragma unroll
-                        for (int q = 0; q < CPL; ++q) u[q] = g[q] * inv;
-                    }
-                    bool bad = false;
+                        for (int k = 0; k < NB; ++k) {
+                            float g[4];
+                            g_blk<CPL>(Gc, P, y, k, s_pr4, s_sg4, g);
 #pragma unroll
-                    for (int q = 0; q < CPL; ++q) bad = bad || !(isfinite(y[q]) && isfinite(g[q]));
+                            for (int c = 0; c < 4; ++c) u[4 * k + c] = g[c] * inv;
+                        }
+                    }
                     if (bad) atomicCAS(P.status, ST_OK, ST_NONFINITE);
                     store(P.y, y);
                     store(P.u, u);
@@ -353,15 +376,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) y[4 * k + c] = y[4 * k + c] / s_sg[4 * j + c];
                         }
-                    g_grad<CPL>(Gc, P, y, g, s_pr, s_sg);
                     ff dl = ff_make(0.0f);
                     const int integ = sH.phase == 0 ? INTEG_LF : sH.integ;
                     const int K = CF.K[integ];
                     auto phi = [&]() {
                         for (int k = 0; k < K; ++k) {
-                            g_b<CPL>(Gc, CF.b[integ][k] * eps, inv_dm1, dm1, g, u, dl);
+                            g_b<CPL>(Gc, P, CF.b[integ][k] * eps, inv_dm1, dm1, y, u, dl, s_pr4, s_sg4);
                             if (k < K - 1) {
-                                const ff dlp = g_a<CPL>(Gc, P, CF.a[integ][k] * eps, y, u, g, s_pr, s_sg);
+                                const ff dlp = g_a<CPL>(Gc, P, CF.a[integ][k] * eps, y, u, s_pr4, s_sg4);
                                 dl = ff_add(dl, ff_neg(dlp));
                             }
                         }
@@ -443,14 +465,16 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                 }
                 // per-coordinate sums of y and y^2 (this thread's own slots)
 #pragma unroll
-                for (int k = 0; k < NB; ++k)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int i = 4 * (Gc.gl + Gc.lpc * k) + c;
-                        const float v = y[4 * k + c];
-                        q0[i] += v;
-                        q1[i] = fmaf(v, v, q1[i]);
-                    }
+                for (int k = 0; k < NB; ++k) {
+                    const int j = Gc.gl + Gc.lpc * k;
+                    float4 a = q0[j], s = q1[j];
+                    const float* v = y + 4 * k;
+                    a.x += v[0]; a.y += v[1]; a.z += v[2]; a.w += v[3];
+                    s.x = fmaf(v[0], v[0], s.x); s.y = fmaf(v[1], v[1], s.y);
+                    s.z = fmaf(v[2], v[2], s.z); s.w = fmaf(v[3], v[3], s.w);
+                    q0[j] = a;
+                    q1[j] = s;
+                }
             }
             if (lane == 0 && Gc.wig == 0)
 #pragma unroll
@@ -561,6 +585,12 @@ cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, co
     e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     void* args[] = {&a};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusNone)
+        return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBT), args, smem, st);
+    // inside a stream capture: the launch-attribute form records a cooperative kernel node
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kBT);

@@ -14,6 +14,7 @@ struct laps_target {
     int kind = 0, d = 0, d_pad = 0;
     float* prec_pad = nullptr;  // GAUSS_DIAG precisions, zero padded to d_pad (owned)
     laps::LogregData lr{};      // LOGREG: padded copies of X and y (owned)
+    int* status = nullptr;      // LOGREG: latched status of the tensor-core target call (owned)
 };
 
 struct laps_ctx {

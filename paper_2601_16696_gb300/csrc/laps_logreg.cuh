@@ -39,6 +39,9 @@ cudaError_t logreg_mma_prepare(LogregData& D);
 cudaError_t logreg_mma_wmap(void* tmW, const void* Wb, int64_t M_pad, int kp);
 // data splits of the launch (every split non-empty) and rows per split
 int logreg_mma_splits(const LogregData& D, int64_t M, int nsm, int* rps);
+// points [M][d] -> FP32 [M][kp] and BF16 hi | lo [M_pad][2 kp] (rows past M untouched)
+cudaError_t logreg_pack_points(const float* x, int64_t M, int d, int kp, float* W32, void* Wb,
+                               cudaStream_t st);
 // gradient partials like logreg_grad_f32; W32 is the FP32 [M][kp] copy of the
 // points (prior terms); a bounded wait that expires sets *status
 cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W32, int64_t M, int S,

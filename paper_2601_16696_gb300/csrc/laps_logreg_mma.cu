@@ -485,7 +485,31 @@ __global__ void to_bf16_kernel(const float* __restrict__ X, __nv_bfloat16* __res
     }
 }
 
+// caller's points [M][d] -> the FP32 [M][kp] copy and the BF16 hi | lo [M_pad][2 kp] copy
+__global__ void pack_points_kernel(const float* __restrict__ x, int64_t M, int d, int kp,
+                                   float* __restrict__ W32, __nv_bfloat16* __restrict__ Wb) {
+    const int64_t n = M * kp;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / kp;
+        const int i = (int)(k - m * kp);
+        const float v = i < d ? x[m * d + i] : 0.0f;
+        W32[k] = v;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        Wb[m * 2 * kp + i] = hi;
+        Wb[m * 2 * kp + kp + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
 }  // namespace
+
+cudaError_t logreg_pack_points(const float* x, int64_t M, int d, int kp, float* W32, void* Wb,
+                               cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((M * kp + 255) / 256, 4096);
+    pack_points_kernel<<<std::max(blocks, 1), 256, 0, st>>>(x, M, d, kp, W32,
+                                                          reinterpret_cast<__nv_bfloat16*>(Wb));
+    return cudaGetLastError();
+}
 
 bool logreg_mma_supported(int kp) { return kp == 64 || kp == 128; }
 

@@ -75,16 +75,23 @@ __global__ void logreg_pack_kernel(const float* __restrict__ x, float* __restric
         W[k] = i < d ? x[m * d + i] : 0.0f;
     }
 }
+// the S partials of the gradient kernel summed in order, back to the caller's [M][d]
 __global__ void logreg_unpack_kernel(const float* __restrict__ G, const float2* __restrict__ lp,
                                      float* __restrict__ grad, float* __restrict__ logp, int64_t M,
-                                     int d, int kp) {
+                                     int d, int kp, int S) {
     const int64_t n = M * d;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = k / d;
         const int i = (int)(k - m * d);
-        grad[k] = G[m * kp + i];
-        if (i == 0) logp[m] = lp[m].x + lp[m].y;
+        float g = 0.0f;
+        for (int s = 0; s < S; ++s) g += G[((size_t)s * M + m) * kp + i];
+        grad[k] = g;
+        if (i == 0) {
+            ff l = ff_make(0.0f);
+            for (int s = 0; s < S; ++s) l = ff_add(l, ff{lp[(size_t)s * M + m].x, lp[(size_t)s * M + m].y});
+            logp[m] = l.hi + l.lo;
+        }
     }
 }
 
@@ -102,7 +109,7 @@ static laps_status logreg_logp_grad(const laps_target* tg, const float* x, int64
         logreg_pack_kernel<<<blocks, 256, 0, st>>>(x, W, M, d, kp);
         rs = streamed_target_grad(tg, W, M, G, lp, st);
         if (rs == LAPS_OK) {
-            logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp);
+            logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp, 1);
             e = cudaGetLastError();
         }
     }
@@ -113,9 +120,71 @@ static laps_status logreg_logp_grad(const laps_target* tg, const float* x, int64
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "LOGREG logp_grad");
 }
 
+// LOGREG on the tensor cores (the mixed-precision form's unadjusted-phase
+// arithmetic: BF16-rounded data, points as two BF16 terms); stream-ordered, a
+// bounded wait that expired is latched in the target's status word
+static laps_status logreg_logp_grad_mixed(const laps_target* tg, const float* x, int64_t M, float* logp,
+                                          float* grad, cudaStream_t st) {
+    const LogregData& L = tg->lr;
+    if (!L.Xb) return fail(LAPS_ERR_UNSUPPORTED, "mixed precision is built for LOGREG with d <= 128");
+    const int kp = L.kp, d = tg->d;
+    const int64_t M_pad = (M + 127) / 128 * 128;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int rps = 64;
+    const int S = logreg_mma_splits(L, M, nsm, &rps);
+    float *W32 = nullptr, *G = nullptr;
+    void* Wb = nullptr;
+    float2* lp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&W32, (size_t)M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&Wb, (size_t)M_pad * 2 * kp * 2, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G, (size_t)S * M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&lp, (size_t)S * M * 8, st);
+    alignas(64) unsigned char tmW[128];
+    if (e == cudaSuccess && M_pad > M)  // the last tile's rows past M stay zero
+        e = cudaMemsetAsync(static_cast<char*>(Wb) + (size_t)M * 2 * kp * 2, 0,
+                            (size_t)(M_pad - M) * 2 * kp * 2, st);
+    if (e == cudaSuccess) e = logreg_pack_points(x, M, d, kp, W32, Wb, st);
+    if (e == cudaSuccess) e = logreg_mma_wmap(tmW, Wb, M_pad, kp);
+    if (e == cudaSuccess) e = logreg_grad_mma(L, tmW, W32, M, S, rps, G, lp, tg->status, 2000000000LL, st);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<int64_t>((M * d + 255) / 256, 4096);
+        logreg_unpack_kernel<<<std::max(blocks, 1), 256, 0, st>>>(G, lp, grad, logp, M, d, kp, S);
+        e = cudaGetLastError();
+    }
+    if (W32) cudaFreeAsync(W32, st);
+    if (Wb) cudaFreeAsync(Wb, st);
+    if (G) cudaFreeAsync(G, st);
+    if (lp) cudaFreeAsync(lp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "LOGREG logp_grad (tensor cores)");
+    return LAPS_OK;
+}
+
 }  // namespace laps
 
 using namespace laps;
+
+extern "C" laps_status laps_target_status(laps_target* tg) {
+    if (!tg) return fail(LAPS_ERR_INVALID_ARG, "null target");
+    if (!tg->status) return LAPS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    int s = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&s, tg->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(tg->status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "laps_target_status");
+    return status_error(s);
+}
+
+extern "C" laps_status laps_target_logp_grad_prec(const laps_target* tg, const float* x, int64_t M,
+                                                  float* logp, float* grad, int precision, void* stream) {
+    if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (precision == LAPS_FP32) return laps_target_logp_grad(tg, x, M, logp, grad, stream);
+    if (precision != LAPS_MIXED) return fail(LAPS_ERR_INVALID_ARG, "unknown precision");
+    if (tg->kind != TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "mixed precision applies to LOGREG only");
+    if (M == 0) return LAPS_OK;
+    return logreg_logp_grad_mixed(tg, x, M, logp, grad, (cudaStream_t)stream);
+}
 
 extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
                                              float* logp, float* grad, void* stream) {

@@ -103,6 +103,8 @@ SIGNATURES = {
     "laps_target_create": (C.c_int, [C.POINTER(TargetDesc), C.POINTER(_vp)]),
     "laps_target_destroy": (None, [_vp]),
     "laps_target_logp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "laps_target_logp_grad_prec": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int, _vp]),
+    "laps_target_status": (C.c_int, [_vp]),
     "laps_create": (C.c_int, [_vp, C.c_int64, C.POINTER(Config), C.POINTER(_vp)]),
     "laps_destroy": (None, [_vp]),
     "laps_init": (C.c_int, [_vp, _vp, C.c_double, C.c_uint64, _vp]),
@@ -220,15 +222,24 @@ class Target:
     def handle(self):
         return self._h
 
-    def logp_grad(self, x: torch.Tensor, stream=None):
-        """log p [M] and grad log p [M, d] of the rows of x (FP32, CUDA)."""
+    def logp_grad(self, x: torch.Tensor, precision: int = 0, stream=None):
+        """log p [M] and grad log p [M, d] of the rows of x (FP32, CUDA);
+        precision 1 (LAPS_MIXED): the tensor-core form of a LOGREG target."""
         x = x.contiguous()
         M = x.shape[0]
         logp = torch.empty(M, dtype=torch.float32, device=x.device)
         grad = torch.empty_like(x)
-        _check(lib().laps_target_logp_grad(self._h, _ptr(x), M, _ptr(logp), _ptr(grad),
-                                           _stream(stream)))
+        if precision == 0:
+            _check(lib().laps_target_logp_grad(self._h, _ptr(x), M, _ptr(logp), _ptr(grad),
+                                               _stream(stream)))
+        else:
+            _check(lib().laps_target_logp_grad_prec(self._h, _ptr(x), M, _ptr(logp), _ptr(grad),
+                                                    precision, _stream(stream)))
         return logp, grad
+
+    def check(self):
+        """Raises LapsError if a kernel of this target latched an error."""
+        _check(lib().laps_target_status(self._h))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -190,6 +190,21 @@ def test_mixed_gradient_vs_oracle_on_bf16_data(L, ora, n, nf, M):
     assert err_lp < 2e-5, err_lp
 
 
+@pytest.mark.parametrize("n,nf,M", [(1000, 100, 300), (129, 40, 1000)])
+def test_mixed_target_call_vs_oracle_on_bf16_data(L, ora, n, nf, M):
+    pr = W.logreg(n_data=n, n_feat=nf, M=M, n_steps=10)
+    rng = np.random.default_rng(9)
+    x = (0.3 * rng.standard_normal((M, pr.d))).astype(np.float32)
+    tg = L.Target.from_problem(pr)
+    lp, g = tg.logp_grad(torch.from_numpy(x).cuda(), precision=1)
+    tg.check()  # no bounded wait expired
+    ot = ora.OracleTarget(pr.kind, pr.d, X=_bf16_round(pr.X), y=pr.y, prior_var=pr.prior_var)
+    lpr, gr = ot.logp_grad(x.astype(np.float64))
+    g = g.double().cpu().numpy()
+    assert np.max(np.abs(g - gr) / np.abs(gr).max(axis=1, keepdims=True)) < 4e-3
+    assert np.max(np.abs(lp.double().cpu().numpy() - lpr) / (np.abs(lpr) + 1.0)) < 2e-5
+
+
 def test_mixed_first_steps_error_stated(L, ora):
     pr = W.logreg(n_data=1000, M=512, n_steps=200)
     s = _gpu(L, pr, seed=3, fixed_eps=0.01, precision=1)
