@@ -101,7 +101,8 @@ def _kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_16696_gb300", "csrc")
-    for f in ("laps_resident_kernel.cuh", "laps_resident.cuh", "laps_device.cuh", "laps_params.h"):
+    for f in ("laps_resident_kernel.cuh", "laps_resident.cuh", "laps_finalise.cuh", "laps_device.cuh",
+              "laps_params.h"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

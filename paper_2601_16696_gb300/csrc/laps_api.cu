@@ -44,16 +44,6 @@ static const void* resident_fn(int kind, int lpc, int cpl) {
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // ------------------------------------------------------------------ small kernels
-__global__ void pack_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t M,
-                                 int d, int d_pad) {
-    const int64_t n = M * (int64_t)d_pad;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = k / d_pad;
-        const int i = (int)(k - m * d_pad);
-        dst[k] = i < d ? src[m * d + i] : 0.0f;
-    }
-}
 __global__ void unpack_rows_kernel(const float* __restrict__ src, const float* __restrict__ scale,
                                    float* __restrict__ dst, int64_t M, int d, int d_pad) {
     const int64_t n = M * (int64_t)d;
@@ -514,8 +504,6 @@ laps_status status_error(int s) {
     if (s == ST_OK) return LAPS_OK;
     if (s == ST_TIMEOUT) return fail(LAPS_ERR_TIMEOUT, "a grid barrier wait exceeded barrier_timeout_ns");
     if (s == ST_NONFINITE) return fail(LAPS_ERR_NONFINITE, "non-finite initial position, log p or gradient");
-    if (s == ST_OVERFLOW)
-        return fail(LAPS_ERR_NONFINITE, "an ensemble sum left the accumulator range (|sum| >= 2^77): the run diverged");
     return fail(LAPS_ERR_CUDA, "device status " + std::to_string(s));
 }
 

@@ -11,7 +11,7 @@
 namespace laps {
 
 // ---------------------------------------------------------------- status codes
-enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5, ST_OVERFLOW = 6 };
+enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5 };
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Ten rounds; each multiplies words 0 and 2 by the round multipliers, xors the
@@ -102,94 +102,6 @@ __device__ __forceinline__ float across_groups(float v) {
     for (int o = LPC; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = (w > v || w != w) ? w : v;  // NaN propagates
-    }
-    return v;
-}
-
-// ---------------------------------------------------------------- fixed point
-// Exact, order-independent accumulation across blocks: a value is converted to
-// a 128-bit two's-complement integer with FX_FRAC = 48 fractional bits
-// (resolution 2^-48 ~ 3.6e-15, range |v| < 2^77 ~ 1.5e23), split into four
-// 32-bit limbs, and each limb is added with a 64-bit integer atomic into its
-// own accumulator.  Integer addition commutes, so the totals, and everything
-// computed from them, are bit-identical from run to run whatever order the
-// blocks arrive in.  A value outside the range (or not finite) raises `bad`.
-constexpr int FX_FRAC = 48;
-struct i128 {
-    unsigned long long lo;
-    long long hi;
-};
-__device__ __forceinline__ i128 f32_to_fx(float f, int& bad) {
-    i128 r{0ull, 0ll};
-    const unsigned b = __float_as_uint(f);
-    const int e = (b >> 23) & 0xff;
-    if (e == 0) return r;  // zero or subnormal: below the resolution
-    if (e == 0xff) { bad = 1; return r; }
-    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // |f| = m 2^(e-150)
-    const int sh = e - 150 + FX_FRAC;  // bit position of m's lsb in |f| 2^FX_FRAC
-    if (sh < 0) {
-        if (sh > -24) r.lo = m >> (-sh);
-    } else if (sh < 64) {
-        r.lo = m << sh;
-        r.hi = (sh > 40) ? (long long)(m >> (64 - sh)) : 0ll;
-    } else if (sh < 64 + 38) {
-        r.hi = (long long)(m << (sh - 64));
-    } else {
-        bad = 1;
-        return r;
-    }
-    if (b >> 31) {  // two's-complement negation
-        r.lo = ~r.lo + 1ull;
-        r.hi = ~r.hi + (r.lo == 0ull ? 1ll : 0ll);
-    }
-    return r;
-}
-__device__ __forceinline__ i128 fx_add(i128 a, i128 b) {
-    i128 r;
-    r.lo = a.lo + b.lo;
-    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ll : 0ll);
-    return r;
-}
-// Each limb accumulator sits alone in a 128-byte line (FX_STRIDE u64 apart):
-// integer atomics to one L2 line serialise, so limbs sharing lines would make
-// every block's additions queue behind each other.
-constexpr int FX_STRIDE = 16;
-// acc: the four limb accumulators of one quantity, FX_STRIDE apart
-__device__ __forceinline__ void fx_atomic_add(unsigned long long* acc, ff v, int& bad) {
-    const i128 x = fx_add(f32_to_fx(v.hi, bad), f32_to_fx(v.lo, bad));
-    atomicAdd(acc + 0 * FX_STRIDE, x.lo & 0xffffffffull);
-    atomicAdd(acc + 1 * FX_STRIDE, x.lo >> 32);
-    atomicAdd(acc + 2 * FX_STRIDE, (unsigned long long)x.hi & 0xffffffffull);
-    atomicAdd(acc + 3 * FX_STRIDE, (unsigned long long)(x.hi >> 32));  // signed limb
-}
-// total of the four limb sums: exact 128-bit integer, then to FP64 (53 bits)
-// and split into a float-float
-__device__ __forceinline__ ff fx_read(const unsigned long long* acc) {
-    const unsigned long long a0 = __ldcg(acc + 0 * FX_STRIDE), a1 = __ldcg(acc + 1 * FX_STRIDE);
-    const unsigned long long a2 = __ldcg(acc + 2 * FX_STRIDE);
-    const long long a3 = (long long)__ldcg(acc + 3 * FX_STRIDE);
-    const unsigned long long t0 = a0;
-    const unsigned long long t1 = a1 + (t0 >> 32);
-    const unsigned long long t2 = a2 + (t1 >> 32);
-    const long long t3 = a3 + (long long)(t2 >> 32);
-    const unsigned long long lo = (t0 & 0xffffffffull) | (t1 << 32);
-    const long long hi = (long long)((t2 & 0xffffffffull) | ((unsigned long long)t3 << 32));
-    // value = (hi 2^64 + lo) 2^-48 = hi 2^16 + lo 2^-48
-    const double v = fma((double)hi, 65536.0, (double)lo * 3.552713678800501e-15);
-    const float h = (float)v;
-    return ff{h, (float)(v - (double)h)};
-}
-
 // ---------------------------------------------------------------- timers, barrier
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -201,17 +113,17 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }
 
-// Grid-wide barrier on a monotone arrival counter (reset to 0 before the
-// launch): barrier number k (k = 1, 2, ...) waits until the counter reaches
-// k * expected.  One atomic per block and a polling read; no reset between
-// barriers.  Bounded exactly like grid_barrier below.
+// Grid-wide barrier for a cooperative launch (all blocks co-resident) on a
+// monotone arrival counter (reset to 0 before the launch): barrier number k
+// (k = 1, 2, ...) waits until the counter reaches k * expected.  One release
+// reduction per block and acquire polling; no reset between barriers.  The
+// wait is bounded: after timeout_ns the block records ST_TIMEOUT in *status
+// and returns false, as does every block that sees a recorded error, so the
+// kernel always terminates.
 __device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, unsigned target,
                                                 long long timeout_ns) {
     __shared__ int s_ok2;
@@ -240,45 +152,6 @@ __device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, un
     }
     __syncthreads();
     return s_ok2 != 0;
-}
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after timeout_ns the block records ST_TIMEOUT in *status
-// and returns false, as does every block that sees a recorded error, so the
-// kernel always terminates.  Returns true when all blocks arrived.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* status,
-                                             unsigned nblocks, long long timeout_ns) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g0 = ld_acquire_u32(gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            *count = 0u;
-            __threadfence();
-            st_release_u32(gen, g0 + 1u);
-        } else {
-            const uint64_t t0 = global_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(gen) == g0) {
-                if ((++spins & 63u) == 0u) {
-                    if (ld_volatile_i32(status) != ST_OK) { ok = 0; break; }
-                    if ((long long)(global_ns() - t0) > timeout_ns) {
-                        atomicCAS(status, ST_OK, ST_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
-        if (ok && ld_volatile_i32(status) != ST_OK) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 }  // namespace laps

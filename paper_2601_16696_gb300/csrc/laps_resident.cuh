@@ -1,23 +1,9 @@
-// laps_resident.cuh -- persistent, register-resident LAPS kernel (sm_103a).
-//
-// One cooperative launch runs many iterations of Algorithm 1.  Each chain is
-// owned by a group of LPC lanes; lane `gl` of the group holds the coordinate
-// blocks j = gl + LPC*k (k < CPL/4) of the chain's position y, velocity u and
-// gradient g in registers for the whole launch.  An iteration is
-//   1. the chain update: an unadjusted step O_{eps/2} Phi_eps O_{eps/2} with
-//      leapfrog (App. E, Eq. "discrete update"), or a MAMS proposal of N such
-//      steps with MN2/MN4 and the accept/reject test (App. F);
-//   2. per-block sums of y, y^2, g, y g over the block's chains and of the
-//      per-chain energy error / acceptance (compensated FP32), added into
-//      global 128-bit fixed-point accumulators with integer atomics (exact,
-//      so the totals do not depend on the order of the blocks);
-//   3. one grid barrier;
-//   4. every block reads the totals (Eq. ECA) and computes, identically, the
-//      per-coordinate Var, V_ii (App. B), the window statistic
-//      delta[x_i^2] (Eq. "relative fluctuations"), b^2 (Eq. "bias") and the
-//      finalise (Sec. 3.1 controller, Eq. "L", the switch of Sec. 4, the
-//      bisection of Sec. 5.1), so all blocks hold bit-identical
-//      hyperparameters without a broadcast or a second barrier.
+// laps_resident.cuh -- the per-chain maps of the LAPS kernels (sm_103a):
+// the targets' log p and gradient in the sampler's coordinates, the O, B and A
+// maps of App. E on a chain held by a group of LPC lanes (CPL coordinates per
+// lane, in registers), the integrator step of Eq. "integrator", the step
+// scalars of an iteration, and float-float helpers.  The register-resident
+// kernel (laps_resident_kernel.cuh) and the streamed path build on these.
 #pragma once
 #include <cmath>
 
