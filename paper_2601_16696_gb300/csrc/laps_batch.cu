@@ -154,70 +154,159 @@ __device__ __forceinline__ void g_blk(const Grp& G, const KParams& P, const floa
     g[3] = sg.w * (-pr.w * (sg.w * y[4 * k + 3]));
 }
 
-// App. E, Eq. "B MCHMC", overflow-free form (zeta = e^-delta)
+// ---------------------------------------------------------------- fused step
+// One step O_{eps/2} Phi_eps O_{eps/2} with three group reductions instead of
+// six: the first O map's |v|^2 is reduced together with g.v and |g|^2 (the
+// first B's g.u is (g.v)/|v|); each A map's log p change together with the
+// next B's |g'|^2 and g'.u; the last O map's |v|^2 together with the
+// non-finite flag of the chain update (when `check`).  Each map is App. E's:
+// O as g_o, B in the overflow-free zeta = e^-delta form, A with the log p
+// change in difference form -1/2 prec (x' - x)(x' + x).
+
+// one float-float and NV (<= 2) floats summed over the group in one pass
+template <int NV>
+__device__ __forceinline__ void gsum_mix(Grp& G, ff& a, float (&v)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = ff_add(a, ff{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if (G.gw == 1) return;
+    float* s = G.red + G.flip * 64;
+    if ((threadIdx.x & 31) == 0) {
+        s[G.wig * 4] = a.hi;
+        s[G.wig * 4 + 1] = a.lo;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[G.wig * 4 + 2 + k] = v[k];
+    }
+    grp_bar(G);
+    ff t{s[0], s[1]};
+    for (int w = 1; w < G.gw; ++w) t = ff_add(t, ff{s[w * 4], s[w * 4 + 1]});
+    a = t;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float x = s[2 + k];
+        for (int w = 1; w < G.gw; ++w) x += s[w * 4 + 2 + k];
+        v[k] = x;
+    }
+    G.flip ^= 1;
+}
+
+// u <- c1 u + c2s Z, not yet normalised; thread partials of |v|^2 (and, with
+// WITH_G, of g.v and |g|^2 with g the gradient at y) into s
+template <int CPL, bool WITH_G>
+__device__ __forceinline__ void g_o_mix(const KParams& P, const Grp& G, uint32_t m, uint32_t t, uint32_t tag,
+                                        float c1, float c2s, float (&u)[CPL], const float (&y)[CPL],
+                                        const float4* s_pr4, const float4* s_sg4, float (&s)[3]) {
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = G.gl + G.lpc * k;
+        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+        float g[4];
+        if (WITH_G) g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[c]) : 0.0f;
+            u[4 * k + c] = v;
+            s[0] = fmaf(v, v, s[0]);
+            if (WITH_G) {
+                s[1] = fmaf(g[c], v, s[1]);
+                s[2] = fmaf(g[c], g[c], s[2]);
+            }
+        }
+    }
+}
+
+// B with its sums |g|^2 and g.u already reduced
 template <int CPL>
-__device__ __forceinline__ void g_b(Grp& G, const KParams& P, float beps, float inv_dm1, float dm1,
-                                    const float (&y)[CPL], float (&u)[CPL], ff& dl, const float4* s_pr4,
-                                    const float4* s_sg4) {
-    float s[2] = {0.0f, 0.0f};
+__device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float beps, float inv_dm1, float dm1,
+                                          float gg, float gu, const float (&y)[CPL], float (&u)[CPL], ff& dl,
+                                          const float4* s_pr4, const float4* s_sg4) {
+    if (!(gg > 0.0f)) return;
+    const float gn = sqrtf(gg);
+    const float eu = gu / gn;
+    const float delta = beps * gn * inv_dm1;
+    const float zeta = expf(-delta);
+    const float om = -expm1f(-delta);
+    const float opz = 1.0f + zeta;
+    const float den = fmaf(eu, om * opz, fmaf(zeta, zeta, 1.0f));
+    const float inv = 1.0f / den;
+    const float cu = 2.0f * zeta * inv;
+    const float ce = om * fmaf(eu, om, opz) * inv / gn;
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         float g[4];
         g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            s[0] = fmaf(g[c], g[c], s[0]);
-            s[1] = fmaf(g[c], u[4 * k + c], s[1]);
-        }
+        for (int c = 0; c < 4; ++c) u[4 * k + c] = fmaf(cu, u[4 * k + c], ce * g[c]);
     }
-    gsum<2>(G, s);
-    const float gg = s[0], gu = s[1];
-    if (gg > 0.0f) {
-        const float gn = sqrtf(gg);
-        const float eu = gu / gn;
-        const float delta = beps * gn * inv_dm1;
-        const float zeta = expf(-delta);
-        const float om = -expm1f(-delta);
-        const float opz = 1.0f + zeta;
-        const float den = fmaf(eu, om * opz, fmaf(zeta, zeta, 1.0f));
-        const float inv = 1.0f / den;
-        const float cu = 2.0f * zeta * inv;
-        const float ce = om * fmaf(eu, om, opz) * inv / gn;
-#pragma unroll
-        for (int k = 0; k < CPL / 4; ++k) {
-            float g[4];
-            g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) u[4 * k + c] = fmaf(cu, u[4 * k + c], ce * g[c]);
-        }
-        dl = ff_add(dl, dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu))));
-    }
+    dl = ff_add(dl, dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu))));
 }
 
-// Gaussian A map: y <- y + ae u and log p(x') - log p(x) in difference form
-// -1/2 prec (x' - x)(x' + x)
 template <int CPL>
-__device__ __forceinline__ ff g_a(Grp& G, const KParams& P, float ae, float (&y)[CPL], const float (&u)[CPL],
-                                  const float4* s_pr4, const float4* s_sg4) {
-    float part = 0.0f;
+__device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF, int integ, float eps, float c1,
+                                       float c2s, uint32_t m, uint32_t t, float (&y)[CPL], float (&u)[CPL], ff& dl,
+                                       float inv_dm1, float dm1, const float4* s_pr4, const float4* s_sg4,
+                                       bool check, bool& bad) {
+    const int K = CF.K[integ];
+    float s[3] = {0.0f, 0.0f, 0.0f};
+    g_o_mix<CPL, true>(P, G, m, t, TAG_O1, c1, c2s, u, y, s_pr4, s_sg4, s);
+    gsum<3>(G, s);
+    float inv = s[0] > 0.0f ? 1.0f / sqrtf(s[0]) : 0.0f;
 #pragma unroll
-    for (int k = 0; k < CPL / 4; ++k) {
-        const int j = G.gl + G.lpc * k;
-        if (j >= P.nblk) continue;
-        const float4 pr4 = s_pr4[j], sg4 = s_sg4[j];
-        const float prs[4] = {pr4.x, pr4.y, pr4.z, pr4.w}, sgs[4] = {sg4.x, sg4.y, sg4.z, sg4.w};
+    for (int q = 0; q < CPL; ++q) u[q] *= inv;
+    float gg = s[2], gu = s[1] * inv;
+    for (int k = 0; k < K; ++k) {
+        g_b_apply<CPL>(G, P, CF.b[integ][k] * eps, inv_dm1, dm1, gg, gu, y, u, dl, s_pr4, s_sg4);
+        if (k < K - 1) {
+            // A map, its log p change (difference form) and the next B's sums
+            const float ae = CF.a[integ][k] * eps;
+            float part = 0.0f, v2[2] = {0.0f, 0.0f};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int q = 4 * k + c;
-            const float pr = prs[c], sg = sgs[c];
-            const float xo = sg * y[q];
-            const float yn = fmaf(ae, u[q], y[q]);
-            const float xn = sg * yn;
-            part = fmaf(-0.5f * pr * (xn - xo), xo + xn, part);
-            y[q] = yn;
+            for (int kb = 0; kb < CPL / 4; ++kb) {
+                const int j = G.gl + G.lpc * kb;
+                if (j >= P.nblk) continue;
+                const float4 pr4 = s_pr4[j], sg4 = s_sg4[j];
+                const float prs[4] = {pr4.x, pr4.y, pr4.z, pr4.w}, sgs[4] = {sg4.x, sg4.y, sg4.z, sg4.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int q = 4 * kb + c;
+                    const float xo = sgs[c] * y[q];
+                    const float yn = fmaf(ae, u[q], y[q]);
+                    const float xn = sgs[c] * yn;
+                    part = fmaf(-0.5f * prs[c] * (xn - xo), xo + xn, part);
+                    y[q] = yn;
+                    const float g = sgs[c] * (-prs[c] * xn);
+                    v2[0] = fmaf(g, g, v2[0]);
+                    v2[1] = fmaf(g, u[q], v2[1]);
+                }
+            }
+            ff dlp = ff_make(part);
+            gsum_mix<2>(G, dlp, v2);
+            dl = ff_add(dl, ff_neg(dlp));
+            gg = v2[0];
+            gu = v2[1];
         }
     }
-    return gsum_ff(G, ff_make(part));
+    float s2[3] = {0.0f, 0.0f, 0.0f};
+    g_o_mix<CPL, false>(P, G, m, t, TAG_O2, c1, c2s, u, y, s_pr4, s_sg4, s2);
+    if (check) {
+        float f = isfinite(dl.hi) ? 0.0f : 1.0f;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+            if (!(isfinite(y[q]) && isfinite(u[q]))) f = 1.0f;
+        float r[2] = {s2[0], f};
+        gsum<2>(G, r);
+        s2[0] = r[0];
+        bad = r[1] > 0.0f;
+    } else {
+        s2[0] = gsum1(G, s2[0]);
+    }
+    inv = s2[0] > 0.0f ? 1.0f / sqrtf(s2[0]) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -378,21 +467,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                         }
                     ff dl = ff_make(0.0f);
                     const int integ = sH.phase == 0 ? INTEG_LF : sH.integ;
-                    const int K = CF.K[integ];
-                    auto phi = [&]() {
-                        for (int k = 0; k < K; ++k) {
-                            g_b<CPL>(Gc, P, CF.b[integ][k] * eps, inv_dm1, dm1, y, u, dl, s_pr4, s_sg4);
-                            if (k < K - 1) {
-                                const ff dlp = g_a<CPL>(Gc, P, CF.a[integ][k] * eps, y, u, s_pr4, s_sg4);
-                                dl = ff_add(dl, ff_neg(dlp));
-                            }
-                        }
-                    };
+                    bool bad = false;
                     if (sH.phase == 0) {
-                        const uint32_t t = (uint32_t)sH.t;
-                        g_o<CPL>(P, Gc, m, t, TAG_O1, c1, c2s, u);
-                        phi();
-                        g_o<CPL>(P, Gc, m, t, TAG_O2, c1, c2s, u);
+                        g_step<CPL>(P, Gc, CF, integ, eps, c1, c2s, m, (uint32_t)sH.t, y, u, dl, inv_dm1, dm1,
+                                    s_pr4, s_sg4, true, bad);
                     } else {
                         // App. F step 2: u uniform on the sphere, then N steps
                         float n2 = 0.0f;
@@ -414,17 +492,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) u[q] *= inv;
                         const uint32_t t0 = (uint32_t)sH.t;
-                        for (int n = 0; n < P.N; ++n) {
-                            g_o<CPL>(P, Gc, m, t0 + n, TAG_O1, c1, c2s, u);
-                            phi();
-                            g_o<CPL>(P, Gc, m, t0 + n, TAG_O2, c1, c2s, u);
-                        }
+                        for (int n = 0; n < P.N; ++n)
+                            g_step<CPL>(P, Gc, CF, integ, eps, c1, c2s, m, t0 + n, y, u, dl, inv_dm1, dm1, s_pr4,
+                                        s_sg4, n == P.N - 1, bad);
                     }
-                    float badf = isfinite(dl.hi) ? 0.0f : 1.0f;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q)
-                        if (!(isfinite(y[q]) && isfinite(u[q]))) badf = 1.0f;
-                    const bool bad = gsum1(Gc, badf) > 0.0f;
                     bool keep = !bad;
                     float a_m = 0.0f;
                     if (sH.phase == 1) {
