@@ -143,6 +143,24 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// SFU approximations in their flush-to-zero forms (the epilogue's arguments
+// are never subnormal: 1 + t lies in [1, 2]; e^{-|z|} below 2^-126 flushes to 0)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -327,6 +345,20 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
         bool ok = true;
         for (int c = 0; c < nc; ++c) {
             const int zb = c & 1;
+            // the labels of data rows row0 .. row0 + 15, loaded before waiting for Z
+            const int row0 = r_begin + c * TNR + 16 * h;
+            const int nlive = min(16, r_end - row0);
+            float yy[16];
+            if (nlive >= 16) {
+#pragma unroll
+                for (int j4 = 0; j4 < 4; ++j4) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(A.y + row0) + j4);
+                    yy[4 * j4] = v.x; yy[4 * j4 + 1] = v.y; yy[4 * j4 + 2] = v.z; yy[4 * j4 + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) yy[j] = j < nlive ? A.y[row0 + j] : 0.0f;
+            }
             if (!mbar_wait(bar(B_ZFULL + zb), (c >> 1) & 1, deadline)) { ok = false; break; }
             tc_fence_after();
             float z[16];
@@ -334,33 +366,21 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_ZEMPTY + zb));
-            // residuals and log-likelihood terms of data rows row0 .. row0 + 15.  Fast
-            // intrinsics (this form serves the unadjusted phase only): t = e^{-|z|},
-            // sigmoid from 1 / (1 + t), softplus = max(z, 0) + log(1 + t)
-            const int row0 = r_begin + c * TNR + 16 * h;
-            const int nlive = min(16, r_end - row0);
+            // residuals and log-likelihood terms.  Fast SFU approximations (this
+            // form serves the unadjusted phase only): t = e^{-|z|}, sigmoid from
+            // 1 / (1 + t), softplus = max(z, 0) + log(1 + t)
             float r[16];
             float lsum = 0.0f;
             auto body = [&](auto full) {
-                float yy[16];
-                if (decltype(full)::value) {
-#pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4) {
-                        const float4 v = __ldg(reinterpret_cast<const float4*>(A.y + row0) + j4);
-                        yy[4 * j4] = v.x; yy[4 * j4 + 1] = v.y; yy[4 * j4 + 2] = v.z; yy[4 * j4 + 3] = v.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) yy[j] = j < nlive ? A.y[row0 + j] : 0.0f;
-                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float zz = z[j];
-                    const float t = __expf(-fabsf(zz));
+                    const float t = ex2_ftz(-1.4426950408889634f * fabsf(zz));  // e^{-|z|}
                     const float opt = 1.0f + t;
-                    const float inv = __fdividef(1.0f, opt);
+                    const float inv = rcp_ftz(opt);
                     const float sig = zz >= 0.0f ? inv : t * inv;
-                    const float term = fmaf(yy[j], zz, -(fmaxf(zz, 0.0f) + __logf(opt)));
+                    const float sp = fmaf(0.6931471805599453f, lg2_ftz(opt), fmaxf(zz, 0.0f));
+                    const float term = fmaf(yy[j], zz, -sp);
                     if (decltype(full)::value) {
                         r[j] = yy[j] - sig;
                         lsum += term;
