@@ -270,7 +270,7 @@ def _forms(flush, stream, mhz, seed0):
     return out
 
 
-def ncu_case():
+def ncu_case(adjusted: bool = False):
     import torch
     from paper_2601_16696_gb300 import build, laps, workloads
     build.build()
@@ -278,8 +278,12 @@ def ncu_case():
     tg = laps.Target.from_problem(pr)
     s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, force_switch_at=WORKLOAD["switch_at"])
     s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)  # resident launch 1
-    s.step(20)                                                                # resident launch 2
-    s.step(200)                                                               # resident launch 3
+    if adjusted:
+        s.step(WORKLOAD["switch_at"])                                         # launch 2: to the switch
+        s.step(10)                                                            # launch 3: 10 proposals
+    else:
+        s.step(20)                                                            # resident launch 2
+        s.step(200)                                                           # resident launch 3
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": pr.name, "t": s.stats()["t"], "launch": s.launch_info()}))
     return 0
@@ -297,11 +301,13 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the workload's launch shape, one launch of 200 unadjusted "
                          "iterations after two others (the case profiled under ncu)")
+    ap.add_argument("--ncu-case-adjusted", action="store_true",
+                    help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.ncu_case:
-        return ncu_case()
+    if args.ncu_case or args.ncu_case_adjusted:
+        return ncu_case(adjusted=args.ncu_case_adjusted)
 
     import torch
     rank, world, local = _rank_env()

@@ -89,7 +89,8 @@ def test_logreg_autograd_vs_finite_differences(L, ora):
 
 
 # ------------------------------------------------------------------ the sampler
-@pytest.mark.parametrize("n,nf,M", [(1000, 100, 512), (300, 30, 77)])
+@pytest.mark.parametrize("n,nf,M", [(1000, 100, 512), (300, 30, 77), (400, 150, 130),
+                                    (200, 240, 33)])
 def test_logreg_first_ten_steps_fixed_step(L, ora, n, nf, M):
     pr = W.logreg(n_data=n, n_feat=nf, M=M, n_steps=200)
     s = _gpu(L, pr, seed=3, fixed_eps=0.01)
