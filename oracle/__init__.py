@@ -54,7 +54,7 @@ class Config(C.Structure):
                 ("n_total_steps", C.c_int), ("steps_per_proposal", C.c_int),
                 ("mn4_min_dim", C.c_int), ("eevpd_centered", C.c_int), ("adjusted", C.c_int),
                 ("force_switch_at", C.c_int), ("fixed_eps", C.c_double),
-                ("round_state_f32", C.c_int)]
+                ("round_state_f32", C.c_int), ("dtilde_K", C.c_int)]
 
 
 class TraceRow(C.Structure):
@@ -98,6 +98,12 @@ def lib():
             L.ora_F.restype = C.c_double
             L.ora_dtilde_diag.argtypes = [C.c_int64, C.c_int64, _dp, _dp]
             L.ora_dtilde_diag.restype = C.c_double
+            L.ora_dtilde_full.argtypes = [C.c_int64, C.c_int64, _dp, _dp, C.c_int, C.c_uint64,
+                                          C.c_uint32, C.c_uint32]
+            L.ora_dtilde_full.restype = C.c_double
+            L.ora_rademacher.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                         C.c_int64]
+            L.ora_rademacher.restype = C.c_double
             L.ora_L_of.argtypes = [C.c_int64, C.c_int64, _dp, C.c_double]
             L.ora_L_of.restype = C.c_double
             L.ora_rel_fluct.argtypes = [C.c_int64, _dp]
@@ -227,6 +233,16 @@ def F(D: float) -> float:
 def dtilde_diag(X: np.ndarray, G: np.ndarray) -> float:
     X, G = _f64(X), _f64(G)
     return lib().ora_dtilde_diag(X.shape[0], X.shape[1], _p(X), _p(G))
+
+
+def dtilde_full(X: np.ndarray, G: np.ndarray, K: int, seed: int = 0, pid: int = 0,
+                t: int = 0) -> float:
+    X, G = _f64(X), _f64(G)
+    return lib().ora_dtilde_full(X.shape[0], X.shape[1], _p(X), _p(G), K, seed, pid, t)
+
+
+def rademacher(seed: int, pid: int, t: int, k: int, d: int) -> np.ndarray:
+    return np.array([lib().ora_rademacher(seed, pid, t, k, i) for i in range(d)])
 
 
 def L_of(X: np.ndarray, alpha: float = 2.0) -> float:

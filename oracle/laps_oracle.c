@@ -292,6 +292,55 @@ double ora_dtilde_diag(int64_t M, int64_t d, const double* X, const double* G) {
     return acc / (double)d;
 }
 
+/* Rademacher entry z_k,i = +1 if bit (i mod 32) of word (i / 32 mod 4) of
+ * Philox(counter (i / 128, k, t, 5 | pid << 8)) is set, else -1. */
+double ora_rademacher(uint64_t seed, uint32_t pid, uint32_t t, uint32_t k, int64_t i) {
+    uint32_t ctr[4] = {(uint32_t)(i / 128), k, t, 5u | (pid << 8)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    ora_philox4x32_10(ctr, key, out);
+    return ((out[(i / 32) % 4] >> (i % 32)) & 1u) ? 1.0 : -1.0;
+}
+
+/* App. B, "Full rank": D~ = |I - V|_F^2 / d with V_ij = -Cov_rho(x_i, d_j log p),
+ * by Hutchinson's trace estimator over K Rademacher vectors z_k (drawn for
+ * step t):  (I - V) z = z + Cov_rho(x, g.z), so
+ *   D~_full = (1/(d K)) sum_k | z_k + (1/M) sum_m (x^m - xbar)(s_mk - sbar_k) |^2,
+ * s_mk = g^m . z_k  (Eq. ECA for the ensemble expectations). */
+double ora_dtilde_full(int64_t M, int64_t d, const double* X, const double* G, int K, uint64_t seed,
+                       uint32_t pid, uint32_t t) {
+    double* z = (double*)malloc((size_t)d * sizeof(double));
+    double* sm = (double*)malloc((size_t)M * sizeof(double));
+    double* xbar = (double*)malloc((size_t)d * sizeof(double));
+    for (int64_t i = 0; i < d; ++i) {
+        double a = 0.0;
+        for (int64_t m = 0; m < M; ++m) a += X[m * d + i];
+        xbar[i] = a / (double)M;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+        for (int64_t i = 0; i < d; ++i) z[i] = ora_rademacher(seed, pid, t, (uint32_t)k, i);
+        double sbar = 0.0;
+        for (int64_t m = 0; m < M; ++m) {
+            double a = 0.0;
+            for (int64_t i = 0; i < d; ++i) a += G[m * d + i] * z[i];
+            sm[m] = a;
+            sbar += a;
+        }
+        sbar /= (double)M;
+        for (int64_t i = 0; i < d; ++i) {
+            double c = 0.0;
+            for (int64_t m = 0; m < M; ++m) c += (X[m * d + i] - xbar[i]) * (sm[m] - sbar);
+            c /= (double)M;
+            acc += (z[i] + c) * (z[i] + c);
+        }
+    }
+    free(z);
+    free(sm);
+    free(xbar);
+    return acc / ((double)d * (double)K);
+}
+
 static double var_col(int64_t M, int64_t d, const double* X, int64_t i) {
     double mx = 0.0;
     for (int64_t m = 0; m < M; ++m) mx += X[m * d + i];
@@ -350,6 +399,7 @@ void ora_config_default(ora_config* c) {
     c->force_switch_at = 0;
     c->fixed_eps = 0.0;
     c->round_state_f32 = 0;
+    c->dtilde_K = 0;
 }
 
 struct ora_state {
@@ -712,7 +762,10 @@ static int iterate_body(ora_state* s, ora_trace_row* row) {
         double* var = (double*)malloc((size_t)d * sizeof(double));
         double sum_var = 0.0;
         for (int64_t i = 0; i < d; ++i) { var[i] = var_col(M, d, s->y, i); sum_var += var[i]; }
-        const double dt = ora_dtilde_diag(M, d, s->y, s->g);
+        const double dt = c->dtilde_K > 0
+                              ? ora_dtilde_full(M, d, s->y, s->g, c->dtilde_K, s->seed, s->pid,
+                                                (uint32_t)(s->t - 1))
+                              : ora_dtilde_diag(M, d, s->y, s->g);
         double eevpd = NAN;
         if (nfin > 0) {
             const double mean = sd / (double)nfin;

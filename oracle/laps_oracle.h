@@ -78,6 +78,12 @@ double ora_F(double D);
 /* diagonal equipartition D~_diag of an ensemble (App. B, "Diagonal");
  * X, G are [M][d] positions and gradients */
 double ora_dtilde_diag(int64_t M, int64_t d, const double* X, const double* G);
+/* full-rank equipartition D~ by Hutchinson's estimator over K Rademacher
+ * vectors of step t (App. B, "Full rank"); the vectors' entries are
+ * ora_rademacher(seed, pid, t, k, i) */
+double ora_rademacher(uint64_t seed, uint32_t pid, uint32_t t, uint32_t k, int64_t i);
+double ora_dtilde_full(int64_t M, int64_t d, const double* X, const double* G, int K, uint64_t seed,
+                       uint32_t pid, uint32_t t);
 /* L = alpha * sqrt(sum_i Var[x_i])  (Eq. "L") */
 double ora_L_of(int64_t M, int64_t d, const double* X, double alpha);
 /* relative fluctuation sigma/mu of the last T values of a series (Eq.
@@ -108,6 +114,8 @@ typedef struct {
     int round_state_f32;      /* 1: round y and u to binary32 after every map and form
                                  logistic-regression logits in binary32, to measure how
                                  binary32 arithmetic perturbs the run (not LAPS) */
+    int dtilde_K;             /* > 0: full-rank D~ with this many Rademacher vectors;
+                                 0: D~_diag (App. B) */
 } ora_config;
 
 void ora_config_default(ora_config* c);

@@ -471,3 +471,52 @@ def test_eevpd_scales_like_eps6(ora):
         ee.append(run.trace[1]["eevpd"])
     slope = math.log2(ee[1] / ee[0])
     assert abs(slope - 6.0) < 0.05, slope
+
+
+# ------------------------------------------------------------------ full-rank D~ (App. B)
+def test_rademacher_stream(ora):
+    z = np.array([ora.rademacher(5, 0, 7, k, 512) for k in range(8)])
+    assert set(np.unique(z)) == {-1.0, 1.0}
+    assert abs(z.mean()) < 0.05
+    assert not np.array_equal(z[0], z[1])
+    assert not np.array_equal(ora.rademacher(5, 0, 7, 0, 64), ora.rademacher(5, 0, 8, 0, 64))
+    assert not np.array_equal(ora.rademacher(5, 0, 7, 0, 64), ora.rademacher(5, 1, 7, 0, 64))
+
+
+def test_dtilde_full_scaled_gaussian(ora):
+    """Exact draws of N(0, s^2 Sigma) against the target N(0, Sigma): I - V = (1 - s^2) I,
+    so D~ = (1 - s^2)^2 (Rademacher |z|^2 = d: no Hutchinson noise), up to the ensemble's
+    off-diagonal noise ~ d / M."""
+    rng = np.random.default_rng(1)
+    d, M, s = 12, 40000, 1.3
+    sig = np.exp(np.linspace(-1.0, 1.0, d))
+    X = rng.standard_normal((M, d)) * sig * s
+    G = -X / sig ** 2
+    want = (1.0 - s * s) ** 2
+    got = ora.dtilde_full(X, G, K=50, seed=3)
+    # Hutchinson's expectation is the ensemble's own |I - V|_F^2 / d (plain numpy)
+    V = -np.cov(X.T, G.T, bias=True)[:d, d:]
+    B = np.eye(d) - V
+    assert abs(got - np.sum(B * B) / d) < 0.02 * want
+    assert abs(got - want) < 0.04 * want + 3.0 * d / M
+    assert abs(ora.dtilde_diag(X, G) - want) < 0.04 * want
+
+
+def test_dtilde_full_correlated_gaussian(ora):
+    """Dense precision P, ensemble covariance C != P^-1: D~_full -> |I - C P|_F^2 / d,
+    which the diagonal proxy (sum of the diagonal terms only) underestimates."""
+    rng = np.random.default_rng(2)
+    d, M = 6, 100000
+    A = rng.standard_normal((d, d))
+    P = A @ A.T / d + np.eye(d)
+    Cv = 0.6 * np.linalg.inv(P) + 0.05 * np.outer(np.ones(d), np.ones(d))
+    # an off-target ensemble mean: V is a covariance, so a missing centring would show
+    X = rng.multivariate_normal(np.full(d, 0.7), Cv, size=M)
+    G = -X @ P
+    B = np.eye(d) - Cv @ P
+    exact_full = np.sum(B * B) / d
+    exact_diag = np.sum(np.diag(B) ** 2) / d
+    assert exact_full > 1.2 * exact_diag
+    got = ora.dtilde_full(X, G, K=400, seed=11)
+    assert abs(got - exact_full) < 0.06 * exact_full, (got, exact_full)
+    assert abs(ora.dtilde_diag(X, G) - exact_diag) < 0.03 * exact_diag
