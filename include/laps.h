@@ -106,6 +106,10 @@ typedef struct {
     int barrier_extra_arrivals;  /* test hook, 0 in use: every grid barrier also waits for
                                     this many arrivals that never come, so its bounded wait
                                     expires and the launch ends with LAPS_ERR_TIMEOUT */
+    int dtilde_K;            /* 0: the diagonal bias proxy D~_diag (App. B, the paper's default);
+                                K > 0: the full-rank D~ by Hutchinson's estimator over K
+                                Rademacher vectors per step (App. B "Full rank"; the paper
+                                uses 100); register-resident targets only */
 } laps_config;
 
 /* Snapshot of the sampler (laps_get_stats). */

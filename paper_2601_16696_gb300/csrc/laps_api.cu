@@ -108,11 +108,15 @@ static int resident_qpp(int d_pad, int threads) {
 }
 // largest slice of coordinates a block owns in the reduction
 static int resident_smax(int d, int G) { return (d + G - 1) / G; }
-static size_t resident_smem(int d_pad, int threads, int lpc, int smax) {
+static size_t resident_smem(int d_pad, int threads, int lpc, int smax, int K) {
     const int nwarps = threads / 32, slots = threads / lpc;
     const int qpp = resident_qpp(d_pad, threads);
-    return (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
-           (size_t)d_pad * sizeof(float) + ((size_t)NQ * smax + NCS) * sizeof(float2);
+    size_t b = (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
+               (size_t)d_pad * sizeof(float) + ((size_t)NQ * smax + NCS) * sizeof(float2);
+    if (K > 0)  // full-rank proxy: slice rows, the chains' y and g, s = g.z, Rademacher words
+        b += ((size_t)smax * K + K) * sizeof(float2) + (size_t)2 * slots * d_pad * sizeof(float) +
+             (size_t)slots * K * sizeof(float) + (size_t)K * ((d_pad + 127) / 128) * 4 * sizeof(uint32_t);
+    return b;
 }
 
 laps_status choose_shape(laps_ctx* c) {
@@ -138,7 +142,7 @@ laps_status choose_shape(laps_ctx* c) {
             if (threads < 32 || threads > kMaxThreads || threads % 32) continue;
             const int cpb = threads / lpc;
             const int G = (int)((c->M + cpb - 1) / cpb);
-            const size_t smem = resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G));
+            const size_t smem = resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G), c->cfg.dtilde_K);
             if (smem > 200 * 1024) continue;
             CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int bps = 0;
@@ -227,6 +231,7 @@ void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, K
     P.qpp = c->qpp;
     P.smax = c->smax;
     P.bar_extra = g.barrier_extra_arrivals;
+    P.dfull_K = g.dtilde_K;
     P.phase_ns = c->phase_ns;
     P.yw = c->yw;
     P.uw = c->uw;
@@ -387,8 +392,11 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     *out = nullptr;
     if (M < 2 || M > (1LL << 30)) return fail(LAPS_ERR_INVALID_ARG, "M must be in [2, 2^30]");
     if (cfg->n_total_steps < 1 || cfg->steps_per_proposal < 1 || !(cfg->window_frac > 0) ||
-        !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0)
+        !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0 || cfg->dtilde_K < 0 ||
+        cfg->dtilde_K > 1024)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
+    if (cfg->dtilde_K > 0 && tg->kind == TGT_LOGREG)
+        return fail(LAPS_ERR_UNSUPPORTED, "the full-rank bias proxy is built for the register-resident targets");
     laps_ctx* c = new laps_ctx();
     c->tg = tg;
     c->M = M;
@@ -408,7 +416,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
               alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp_ff, M * 8) &&
               alloc((void**)&c->sigma, c->d_pad * 4) &&
-              alloc((void**)&c->part, ((size_t)NQ * c->d_pad + NCS) * c->G * 8) &&
+              alloc((void**)&c->part, rows_total(c->d_pad, cfg->dtilde_K) * c->G * 8) &&
               alloc((void**)&c->cstat, (size_t)c->d_pad * NCO * 4) &&
               alloc((void**)&c->ctot, (size_t)NCS * 8) &&
               alloc((void**)&c->ring, (size_t)(c->T + 1) * c->d_pad * 8) &&

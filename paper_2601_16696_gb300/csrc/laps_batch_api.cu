@@ -217,6 +217,7 @@ laps_status laps_batch_create(const laps_problem* probs, int n, const laps_confi
     if (cfg->n_total_steps < 1 || cfg->steps_per_proposal < 1 || !(cfg->window_frac > 0) ||
         !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
+    if (cfg->dtilde_K != 0) return fail(LAPS_ERR_UNSUPPORTED, "the batch serves the diagonal bias proxy");
     for (int k = 0; k < n; ++k) {
         const laps_problem& q = probs[k];
         if (q.d < 2 || q.d > kMaxD) return fail(LAPS_ERR_INVALID_ARG, "problem d must be in [2, 10240]");

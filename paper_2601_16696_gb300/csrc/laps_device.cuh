@@ -62,6 +62,16 @@ __device__ __forceinline__ void normals4(uint32_t j, uint32_t m, uint32_t t, uin
     z[3] = rad * s;
 }
 
+// Rademacher entry z_k,i (full-rank bias proxy) of step t: bit (i mod 32) of word
+// (i / 32 mod 4) of Philox(counter (i / 128, k, t, 5 | pid << 8)); set means +1.
+__device__ __forceinline__ float rademacher(uint32_t i, uint32_t k, uint32_t t, uint32_t pid,
+                                            uint32_t k0, uint32_t k1) {
+    const uint4 r = philox4x32_10(make_uint4(i >> 7, k, t, 5u | (pid << 8)), k0, k1);
+    const uint32_t sel = (i >> 5) & 3u;
+    const uint32_t w = sel == 0 ? r.x : sel == 1 ? r.y : sel == 2 ? r.z : r.w;
+    return ((w >> (i & 31u)) & 1u) ? 1.0f : -1.0f;
+}
+
 // ---------------------------------------------------------------- float-float
 struct ff {
     float hi, lo;

@@ -25,7 +25,7 @@ __device__ __forceinline__ float fmax_nan(float a, float b) { return (b > a || b
 
 // block-shared scratch and outputs of ens_gather
 struct FinShared {
-    ff wsum[3][kMaxThreads / 32];    // per-warp sums: Var x, (1 - V)^2, b^2
+    ff wsum[4][kMaxThreads / 32];    // per-warp sums: Var x, (1 - V)^2, b^2, full-rank terms
     float wmax[2][kMaxThreads / 32];  // per-warp maxima: delta, b^2
     int sw;                           // 1: this iteration switched to the adjusted phase
     float eps, c1, c2s;               // step scalars of the next iteration
@@ -38,9 +38,11 @@ __device__ __forceinline__ int ens_nq(const KParams& P, const Hyper& H) {
     return (P.gauss_derived || (H.phase == 1 && P.mode == 1)) ? 2 : NQ;
 }
 
-// Step 3.  s_q: shared [NQ][P.smax] + [NCS] float-float.  All threads of the block call it.
+// Step 3.  s_q: shared [NQ][P.smax] + [NCS] float-float; s_fr (full-rank proxy
+// only, else nullptr): shared [P.smax K + K] float-float.  All threads of the
+// block call it.
 __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* s_q, int bs,
-                                          int nsb) {
+                                          int nsb, ff* s_fr = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int G = P.G, dp = P.d_pad;
@@ -136,6 +138,42 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
         const ff v = s_q[NQ * P.smax + tid];
         P.ctot[tid] = make_float2(v.hi, v.lo);
     }
+    if (P.dfull_K > 0 && s_fr != nullptr && P.mode == 1 && H.phase == 0) {
+        // App. B "Full rank": c_ik = Cov(y_i, s_k) with s_mk = g^m . z_k; the slice's
+        // coordinates receive sum_k (z_ki + c_ik)^2 (Hutchinson over the K vectors)
+        const int K = P.dfull_K;
+        const int nrow = ns * K + K;
+        for (int r = warp; r < nrow; r += nwarps) {
+            const size_t row = r < ns * K ? rows_fb(dp) + (size_t)(i0 + r / K) * K + (r % K)
+                                          : rows_fs(dp, K) + (size_t)(r - ns * K);
+            const float2* src = P.part + row * G;
+            ff s = ff_make(0.0f);
+            for (int c = lane; c < G; c += 32) {
+                const float2 v = __ldcg(src + c);
+                s = ff_add(s, ff{v.x, v.y});
+            }
+            s = group_sum_ff<32>(s);
+            if (lane == 0) s_fr[r] = s;
+        }
+        __syncthreads();
+        for (int kk = warp; kk < ns; kk += nwarps) {
+            const int i = i0 + kk;
+            // the difference E[y s] - ybar sbar is taken in binary64 (a few
+            // operations per coordinate and vector)
+            const double iMd = 1.0 / (double)P.M;
+            const double ybar = ff_to_double(s_q[kk]) * iMd;
+            float acc = 0.0f;
+            for (int k = lane; k < K; k += 32) {
+                const float z = rademacher((uint32_t)i, (uint32_t)k, (uint32_t)H.t, P.pid, P.seed_lo, P.seed_hi);
+                const double c = ff_to_double(s_fr[kk * K + k]) * iMd - ybar * (ff_to_double(s_fr[ns * K + k]) * iMd);
+                const float zc = (float)((double)z + c);
+                acc = fmaf(zc, zc, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) P.cstat[(size_t)i * NCO + CO_DFULL] = acc;
+        }
+    }
 }
 
 // Steps 4-5.  Reads the per-coordinate results (s_var receives Var y_i) and
@@ -148,8 +186,9 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
     float2 tot_pre = make_float2(0.0f, 0.0f);  // warp 0, lanes < NCS: the chain totals
     if (warp == 0 && lane < NCS) tot_pre = __ldcg(P.ctot + lane);
     {
-        ff a_var = ff_make(0.0f), a_dv = ff_make(0.0f), a_b2 = ff_make(0.0f);
+        ff a_var = ff_make(0.0f), a_dv = ff_make(0.0f), a_b2 = ff_make(0.0f), a_df = ff_make(0.0f);
         float a_del = 0.0f, a_b2m = 0.0f;
+        const bool full = P.dfull_K > 0 && P.mode == 1 && H.phase == 0;
         for (int i = tid; i < P.d; i += blockDim.x) {
             const float* co = P.cstat + (size_t)i * NCO;
             const float vy = __ldcg(co + CO_VARY), vx = __ldcg(co + CO_VARX);
@@ -159,6 +198,7 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
             a_var = ff_add(a_var, vx);
             a_dv = ff_add(a_dv, dv);
             a_b2 = ff_add(a_b2, b2);
+            if (full) a_df = ff_add(a_df, __ldcg(co + CO_DFULL));
             a_del = fmax_nan(a_del, del);
             a_b2m = fmax_nan(a_b2m, b2);
         }
@@ -168,9 +208,11 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
             const ff w0{__shfl_xor_sync(0xffffffffu, a_var.hi, o), __shfl_xor_sync(0xffffffffu, a_var.lo, o)};
             const ff w1{__shfl_xor_sync(0xffffffffu, a_dv.hi, o), __shfl_xor_sync(0xffffffffu, a_dv.lo, o)};
             const ff w3{__shfl_xor_sync(0xffffffffu, a_b2.hi, o), __shfl_xor_sync(0xffffffffu, a_b2.lo, o)};
+            const ff w4{__shfl_xor_sync(0xffffffffu, a_df.hi, o), __shfl_xor_sync(0xffffffffu, a_df.lo, o)};
             a_var = ff_add(a_var, w0);
             a_dv = ff_add(a_dv, w1);
             a_b2 = ff_add(a_b2, w3);
+            a_df = ff_add(a_df, w4);
             a_del = fmax_nan(a_del, __shfl_xor_sync(0xffffffffu, a_del, o));
             a_b2m = fmax_nan(a_b2m, __shfl_xor_sync(0xffffffffu, a_b2m, o));
         }
@@ -178,6 +220,7 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
             FS.wsum[0][warp] = a_var;
             FS.wsum[1][warp] = a_dv;
             FS.wsum[2][warp] = a_b2;
+            FS.wsum[3][warp] = a_df;
             FS.wmax[0][warp] = a_del;
             FS.wmax[1][warp] = a_b2m;
         }
@@ -185,12 +228,13 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
     __syncthreads();
     if (warp == 0) {
         // the per-warp partials combined by a butterfly over warp 0's lanes
-        ff v0 = ff_make(0.0f), v1 = v0, v3 = v0;
+        ff v0 = ff_make(0.0f), v1 = v0, v3 = v0, v5 = v0;
         float v2 = 0.0f, v4 = 0.0f;
         if (lane < nwarps) {
             v0 = FS.wsum[0][lane];
             v1 = FS.wsum[1][lane];
             v3 = FS.wsum[2][lane];
+            v5 = FS.wsum[3][lane];
             v2 = FS.wmax[0][lane];
             v4 = FS.wmax[1][lane];
         }
@@ -199,9 +243,11 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
             const ff w0{__shfl_xor_sync(0xffffffffu, v0.hi, o), __shfl_xor_sync(0xffffffffu, v0.lo, o)};
             const ff w1{__shfl_xor_sync(0xffffffffu, v1.hi, o), __shfl_xor_sync(0xffffffffu, v1.lo, o)};
             const ff w3{__shfl_xor_sync(0xffffffffu, v3.hi, o), __shfl_xor_sync(0xffffffffu, v3.lo, o)};
+            const ff w5{__shfl_xor_sync(0xffffffffu, v5.hi, o), __shfl_xor_sync(0xffffffffu, v5.lo, o)};
             v0 = ff_add(v0, w0);
             v1 = ff_add(v1, w1);
             v3 = ff_add(v3, w3);
+            v5 = ff_add(v5, w5);
             v2 = fmax_nan(v2, __shfl_xor_sync(0xffffffffu, v2, o));
             v4 = fmax_nan(v4, __shfl_xor_sync(0xffffffffu, v4, o));
         }
@@ -227,7 +273,8 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
                     const ff sq2 = ff_divf(tot[CS_DSQ], nfin);
                     eevpd = ff_f(P.eevpd_centered ? ff_add(sq2, ff_neg(ff_mul(mean, mean))) : sq2) / d;
                 }
-                const float D = ff_f(v1) / d;
+                // App. B: the diagonal proxy, or the full-rank one (Hutchinson over K vectors)
+                const float D = P.dfull_K > 0 ? ff_f(v5) / (d * (float)P.dfull_K) : ff_f(v1) / d;
                 const float cd = P.C * D, rt = sqrtf(cd);
                 const float wanted = 4.0f * cd * rt / ((1.0f + rt) * (1.0f + rt));
                 h.eps_used = h.eps;

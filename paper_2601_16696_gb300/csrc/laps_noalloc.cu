@@ -91,6 +91,7 @@ extern "C" laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M,
     if (cfg->n_total_steps < 1 || cfg->steps_per_proposal < 1 || !(cfg->window_frac > 0) ||
         !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
+    if (cfg->dtilde_K != 0) return fail(LAPS_ERR_UNSUPPORTED, "laps_run_noalloc serves the diagonal bias proxy");
     if ((x0 && reinterpret_cast<uintptr_t>(x0) % 4) || reinterpret_cast<uintptr_t>(x_out) % 4)
         return fail(LAPS_ERR_INVALID_ARG, "x0 and x_out must be 4-byte aligned");
     switch (desc->kind) {

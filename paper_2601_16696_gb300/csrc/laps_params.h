@@ -22,7 +22,7 @@ struct Hyper {
 
 enum : int { TGT_GAUSS = 0, TGT_BANANA = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3 };
 enum : int { INTEG_LF = 0, INTEG_MN2 = 1, INTEG_MN4 = 2 };
-enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4 };
+enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4, TAG_Z = 5 };
 
 // per-coordinate sums (y, y^2, g, y g) and per-chain sums kept per iteration
 enum : int { NQ = 4 };
@@ -84,7 +84,18 @@ struct KParams {
     int* go;                  // [2]: the iteration is live; it switched to the adjusted phase
     void* Wb;                 // mixed precision: [M_pad][2 d_pad] BF16 (hi | lo) copy of W
     int gauss_derived;        // batched diagonal Gaussians: only y, y^2 are summed per coordinate
+    int dfull_K;              // > 0: full-rank D~ over this many Rademacher vectors (else diagonal)
 };
+
+// per-coordinate result slot of the full-rank bias proxy: sum_k (z_ki + c_ik)^2
+enum : int { CO_DFULL = 5 };
+// rows of the per-block columns: NQ d_pad coordinate rows, NCS chain rows, then
+// (full rank) d_pad K rows of sum_m y_i s_mk and K rows of sum_m s_mk
+__host__ __device__ inline size_t rows_fb(int d_pad) { return (size_t)NQ * d_pad + NCS; }
+__host__ __device__ inline size_t rows_fs(int d_pad, int K) { return rows_fb(d_pad) + (size_t)d_pad * K; }
+__host__ __device__ inline size_t rows_total(int d_pad, int K) {
+    return K > 0 ? rows_fs(d_pad, K) + (size_t)K : rows_fb(d_pad);
+}
 
 // one launch of the streamed path's chain-update kernel: the maps it applies,
 // in this order, to every chain (App. E "discrete update", App. F)

@@ -69,6 +69,13 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     float* s_cs = sq + (size_t)P.qpp * nwarps * dp;                   // [slots][NCSF]
     float* s_var = s_cs + (size_t)slots * NCSF;                       // [dp] Var y (switch)
     ff* s_q = reinterpret_cast<ff*>(s_var + dp);                      // [NQ][smax] + [NCS]
+    // full-rank bias proxy only (App. B "Full rank", K Rademacher vectors)
+    const int KF = P.dfull_K, nb128 = (dp + 127) / 128;
+    ff* s_fr = s_q + (size_t)NQ * P.smax + NCS;                       // [smax K + K]
+    float* f_y = reinterpret_cast<float*>(s_fr + (size_t)P.smax * KF + KF);  // [slots][dp]
+    float* f_g = f_y + (size_t)slots * dp;                            // [slots][dp]
+    float* f_s = f_g + (size_t)slots * dp;                            // [slots][K]
+    uint32_t* f_z = reinterpret_cast<uint32_t*>(f_s + (size_t)slots * KF);  // [K][nb128][4]
 
     if (tid == 0) {
         H = *P.hyper;
@@ -275,13 +282,65 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             s = group_sum_ff<32>(s);
             if (lane == 0) P.part[((size_t)NQ * dp + k) * G + blockIdx.x] = make_float2(s.hi, s.lo);
         }
+        if (KF > 0 && P.mode == 1 && H.phase == 0) {
+            // App. B "Full rank": this block's sum_m y_i s_mk and sum_m s_mk with
+            // s_mk = g^m . z_k, as two small block products on shared memory
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int j = gl + LPC * k;
+                if (j < P.nblk)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        f_y[(size_t)slot * dp + 4 * j + c] = active ? y[4 * k + c] : 0.0f;
+                        f_g[(size_t)slot * dp + 4 * j + c] = active ? g[4 * k + c] : 0.0f;
+                    }
+            }
+            for (int w = tid; w < KF * nb128; w += blockDim.x) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)(w % nb128), (uint32_t)(w / nb128),
+                                                         (uint32_t)H.t, TAG_Z | (P.pid << 8)),
+                                              P.seed_lo, P.seed_hi);
+                uint32_t* zw = f_z + (size_t)w * 4;
+                zw[0] = r.x; zw[1] = r.y; zw[2] = r.z; zw[3] = r.w;
+            }
+            __syncthreads();
+            for (int o = tid; o < slots * KF; o += blockDim.x) {
+                const int sl = o / KF, k = o - sl * KF;
+                const float* gs = f_g + (size_t)sl * dp;
+                const uint32_t* zk = f_z + (size_t)k * nb128 * 4;
+                float acc = 0.0f;
+                for (int i = 0; i < P.d; ++i) {
+                    const bool plus = (zk[i >> 5] >> (i & 31)) & 1u;
+                    acc += plus ? gs[i] : -gs[i];
+                }
+                f_s[o] = acc;
+            }
+            __syncthreads();
+            const size_t rb = rows_fb(dp), rs = rows_fs(dp, KF);
+            // exact products (fma residual) summed in float-float: the covariance
+            // is a small difference of E[y s] and ybar sbar
+            for (int o = tid; o < P.d * KF; o += blockDim.x) {
+                const int i = o / KF, k = o - i * KF;
+                ff acc = ff_make(0.0f);
+                for (int sl = 0; sl < slots; ++sl) {
+                    const float a = f_y[(size_t)sl * dp + i], b = f_s[(size_t)sl * KF + k];
+                    const float p = a * b;
+                    acc = ff_add(acc, ff{p, fmaf(a, b, -p)});
+                }
+                P.part[(rb + (size_t)i * KF + k) * G + blockIdx.x] = make_float2(acc.hi, acc.lo);
+            }
+            for (int k = tid; k < KF; k += blockDim.x) {
+                ff acc = ff_make(0.0f);
+                for (int sl = 0; sl < slots; ++sl) acc = ff_add(acc, f_s[(size_t)sl * KF + k]);
+                P.part[(rs + k) * G + blockIdx.x] = make_float2(acc.hi, acc.lo);
+            }
+        }
         LAPS_PHASE_MARK(3);
         // ------------------------------------------------ 3. barrier, then this block's slice
         n_bar += 1;
         if (!grid_sync_count(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns))
             return;
         LAPS_PHASE_MARK(4);
-        ens_slice(P, H, s_q, blockIdx.x, G);
+        ens_slice(P, H, s_q, blockIdx.x, G, KF > 0 ? s_fr : nullptr);
         LAPS_PHASE_MARK(5);
         // ------------------------------------------------ 4. barrier, then every block gathers
         n_bar += 1;

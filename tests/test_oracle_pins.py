@@ -520,3 +520,24 @@ def test_dtilde_full_correlated_gaussian(ora):
     got = ora.dtilde_full(X, G, K=400, seed=11)
     assert abs(got - exact_full) < 0.06 * exact_full, (got, exact_full)
     assert abs(ora.dtilde_diag(X, G) - exact_diag) < 0.03 * exact_diag
+
+
+def test_dtilde_noise_floor_wishart(ora):
+    """Both proxies on exact draws of the target itself (N(0, I), g = -x): V is
+    the ensemble covariance S (a Wishart matrix over M - 1 degrees of freedom,
+    normalised by M), so the finite-M floor of the proxies is fixed by its
+    moments, E (S_ij - delta_ij)^2 = ((M - 1)(1 + delta_ij) + delta_ij) / M^2:
+      D~_full -> ((M - 1)(d + 1) + 1) / M^2,   D~_diag -> (2 (M - 1) + 1) / M^2.
+    The full-rank floor grows with d (every off-diagonal covariance is noise)."""
+    rng = np.random.default_rng(0)
+    d, M, reps = 20, 200, 60
+    full, diag = [], []
+    for r in range(reps):
+        X = rng.standard_normal((M, d))
+        full.append(ora.dtilde_full(X, -X, K=50, seed=r))
+        diag.append(ora.dtilde_diag(X, -X))
+    want_full = ((M - 1) * (d + 1) + 1) / M ** 2
+    want_diag = (2 * (M - 1) + 1) / M ** 2
+    for v, want in ((np.array(full), want_full), (np.array(diag), want_diag)):
+        se = v.std() / np.sqrt(reps)
+        assert abs(v.mean() - want) < 4.0 * se + 1e-3 * want, (v.mean(), want, se)
