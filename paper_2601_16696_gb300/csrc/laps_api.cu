@@ -11,9 +11,9 @@
 #include "laps_internal.h"
 
 namespace laps {
-const void* resident_kernel_0(int lpc, int cpl);
-const void* resident_kernel_1(int lpc, int cpl);
-const void* resident_kernel_2(int lpc, int cpl);
+const void* resident_kernel_0(int lpc, int cpl, bool fr);
+const void* resident_kernel_1(int lpc, int cpl, bool fr);
+const void* resident_kernel_2(int lpc, int cpl, bool fr);
 
 static thread_local std::string g_err;
 
@@ -32,11 +32,11 @@ laps_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
-static const void* resident_fn(int kind, int lpc, int cpl) {
+static const void* resident_fn(int kind, int lpc, int cpl, bool fr) {
     switch (kind) {
-    case TGT_GAUSS: return resident_kernel_0(lpc, cpl);
-    case TGT_BANANA: return resident_kernel_1(lpc, cpl);
-    case TGT_FUNNEL: return resident_kernel_2(lpc, cpl);
+    case TGT_GAUSS: return resident_kernel_0(lpc, cpl, fr);
+    case TGT_BANANA: return resident_kernel_1(lpc, cpl, fr);
+    case TGT_FUNNEL: return resident_kernel_2(lpc, cpl, fr);
     }
     return nullptr;
 }
@@ -113,10 +113,7 @@ static size_t resident_smem(int d_pad, int threads, int lpc, int smax, int K) {
     const int qpp = resident_qpp(d_pad, threads);
     size_t b = (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
                (size_t)d_pad * sizeof(float) + ((size_t)NQ * smax + NCS) * sizeof(float2);
-    if (K > 0)  // full-rank proxy: slice rows, the chains' y and g, s = g.z, Rademacher words
-        b += ((size_t)smax * K + K) * sizeof(float2) + (size_t)2 * slots * d_pad * sizeof(float) +
-             (size_t)slots * K * sizeof(float) + (size_t)K * ((d_pad + 127) / 128) * 4 * sizeof(uint32_t);
-    return b;
+    return b + fullrank_smem(d_pad, slots, smax, K, threads);
 }
 
 laps_status choose_shape(laps_ctx* c) {
@@ -133,13 +130,15 @@ laps_status choose_shape(laps_ctx* c) {
         if (lpc * cpl < c->d_pad) continue;
         if (c->cfg.lanes_per_chain && lpc != c->cfg.lanes_per_chain) continue;
         if (c->cfg.coords_per_lane && cpl != c->cfg.coords_per_lane) continue;
-        const void* fn = resident_fn(kind, lpc, cpl);
+        const void* fn = resident_fn(kind, lpc, cpl, c->cfg.dtilde_K > 0);
         if (!fn) continue;
         std::vector<int> tlist;
         if (c->cfg.chains_per_block > 0) tlist.push_back(c->cfg.chains_per_block * lpc);
         else tlist = {128, 256, 512};
         for (int threads : tlist) {
             if (threads < 32 || threads > kMaxThreads || threads % 32) continue;
+            // the full-rank proxy keeps one coordinate of its shifts per thread
+            if (c->cfg.dtilde_K > 0 && threads < c->d_pad) continue;
             const int cpb = threads / lpc;
             const int G = (int)((c->M + cpb - 1) / cpb);
             const size_t smem = resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G), c->cfg.dtilde_K);
@@ -168,7 +167,7 @@ laps_status choose_shape(laps_ctx* c) {
     c->smem = best.smem;
     c->qpp = resident_qpp(c->d_pad, best.threads);
     c->smax = resident_smax(c->d, best.G);
-    c->fn = resident_fn(kind, best.lpc, best.cpl);
+    c->fn = resident_fn(kind, best.lpc, best.cpl, c->cfg.dtilde_K > 0);
     return LAPS_OK;
 }
 
@@ -416,7 +415,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     bool ok = alloc((void**)&c->y, Md * 4) && alloc((void**)&c->u, Md * 4) &&
               alloc((void**)&c->g, Md * 4) && alloc((void**)&c->logp_ff, M * 8) &&
               alloc((void**)&c->sigma, c->d_pad * 4) &&
-              alloc((void**)&c->part, rows_total(c->d_pad, cfg->dtilde_K) * c->G * 8) &&
+              alloc((void**)&c->part, part_bytes(c->d_pad, c->G, cfg->dtilde_K)) &&
               alloc((void**)&c->cstat, (size_t)c->d_pad * NCO * 4) &&
               alloc((void**)&c->ctot, (size_t)NCS * 8) &&
               alloc((void**)&c->ring, (size_t)(c->T + 1) * c->d_pad * 8) &&
@@ -711,14 +710,14 @@ laps_status laps_restore(laps_ctx* c, const void* blob, size_t size) {
 // diagnostic build only (not part of the ABI): per-phase device time of block 0
 laps_status laps_debug_phase_ns(laps_ctx* c, unsigned long long* out) {
     if (!c->phase_ns) {
-        CK(cudaMalloc(&c->phase_ns, 8 * sizeof(unsigned long long)));
+        CK(cudaMalloc(&c->phase_ns, 16 * sizeof(unsigned long long)));
         c->allocs.push_back(c->phase_ns);
-        CK(cudaMemset(c->phase_ns, 0, 8 * sizeof(unsigned long long)));
+        CK(cudaMemset(c->phase_ns, 0, 16 * sizeof(unsigned long long)));
     }
-    if (out) {
+    if (out) {  // [16]: the iteration's phases (0-6), the full-rank sub-steps (8-11)
         CK(cudaStreamSynchronize(c->last_stream));
-        CK(cudaMemcpy(out, c->phase_ns, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-        CK(cudaMemset(c->phase_ns, 0, 8 * sizeof(unsigned long long)));
+        CK(cudaMemcpy(out, c->phase_ns, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(c->phase_ns, 0, 16 * sizeof(unsigned long long)));
     }
     return LAPS_OK;
 }

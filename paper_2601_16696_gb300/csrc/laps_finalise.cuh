@@ -41,6 +41,22 @@ __device__ __forceinline__ int ens_nq(const KParams& P, const Hyper& H) {
 // Step 3.  s_q: shared [NQ][P.smax] + [NCS] float-float; s_fr (full-rank proxy
 // only, else nullptr): shared [P.smax K + K] float-float.  All threads of the
 // block call it.
+// Sum of src[c] over c = c0, c0 + step, ... < n (float-float pairs), added in
+// that order; the loads are issued eight at a time so that their L2 latencies
+// overlap.
+__device__ __forceinline__ ff lane_col_sum(const float2* __restrict__ src, int n, int c0, int step) {
+    ff s = ff_make(0.0f);
+    for (int c = c0; c < n; c += 8 * step) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = c + u * step < n ? __ldcg(src + c + u * step) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c + u * step < n) s = ff_add(s, ff{v[u].x, v[u].y});
+    }
+    return s;
+}
+
 __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* s_q, int bs,
                                           int nsb, ff* s_fr = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -55,10 +71,25 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
     const int win_n = H.win_n;
     // the window values this thread will update, loaded before the reductions
     float4 w_pre = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float2 o_pre = make_float2(0.0f, 0.0f);
-    if (push && tid < ns) {
-        w_pre = P.win_sums[i0 + tid];
-        if (win_n >= P.T) o_pre = P.ring[(size_t)((win_n - P.T) % (P.T + 1)) * dp + i0 + tid];
+    float2 o_pre = make_float2(0.0f, 0.0f), e_pre = make_float2(0.0f, 0.0f);
+    float sg_pre = 1.0f, pr_pre = 0.0f, iv_pre = 0.0f;
+    // full-rank proxy: the means this iteration's block products were shifted by,
+    // kept before this slice replaces them with the current means
+    const bool fr_live = P.dfull_K > 0 && s_fr != nullptr;
+    float* s_old = fr_live ? reinterpret_cast<float*>(s_fr + 2 * blockDim.x) : nullptr;  // [ns]
+    if (tid < ns) {
+        const int i = i0 + tid;
+        if (fr_live) s_old[tid] = __ldcg(P.cstat + (size_t)i * NCO + CO_MY);
+        if (push) {
+            w_pre = P.win_sums[i];
+            if (win_n >= P.T) o_pre = P.ring[(size_t)((win_n - P.T) % (P.T + 1)) * dp + i];
+        }
+        sg_pre = P.sigma[i];
+        if (P.gauss_derived) pr_pre = P.prec[i];
+        if (P.Ex2) {
+            e_pre = P.Ex2[i];
+            iv_pre = P.inv_varx2[i];
+        }
     }
     // column sums over the blocks, in block order: one warp per (quantity, coordinate)
     const int n_pairs = nq * ns + (chain_owner ? NCS : 0);
@@ -66,12 +97,7 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
         size_t row;
         if (pidx < nq * ns) row = (size_t)(pidx / ns) * dp + i0 + (pidx % ns);
         else row = (size_t)NQ * dp + (pidx - nq * ns);
-        const float2* src = P.part + row * G;
-        ff s = ff_make(0.0f);
-        for (int c = lane; c < G; c += 32) {
-            const float2 v = __ldcg(src + c);
-            s = ff_add(s, ff{v.x, v.y});
-        }
+        ff s = lane_col_sum(P.part + row * G, G, lane, 32);
         s = group_sum_ff<32>(s);
         if (lane == 0) {
             if (pidx < nq * ns) s_q[(pidx / ns) * P.smax + (pidx % ns)] = s;
@@ -85,7 +111,7 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
         const ff mean = ff_mulf(s_q[0 * P.smax + k], iM);
         const ff ey2 = ff_mulf(s_q[1 * P.smax + k], iM);
         const float var_y = ff_f(ff_add(ey2, ff_neg(ff_mul(mean, mean))));
-        const float sgi = P.sigma[i];
+        const float sgi = k == tid ? sg_pre : P.sigma[i];
         const float s2i = sgi * sgi;
         const ff ex2 = ff_mulf(ey2, s2i);
         float dv = 0.0f, del = 0.0f, b2 = 0.0f;
@@ -97,7 +123,7 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
             dv = (1.0f - V) * (1.0f - V);
         } else if (P.gauss_derived && (P.mode == 0 || H.phase == 0)) {
             // diagonal Gaussian: g_i = -prec_i sigma_i^2 y_i, so V_ii = prec_i sigma_i^2 Var[y_i]
-            const float V = P.prec[i] * s2i * var_y;
+            const float V = (k == tid ? pr_pre : P.prec[i]) * s2i * var_y;
             dv = (1.0f - V) * (1.0f - V);
         }
         if (push) {
@@ -123,11 +149,15 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
             }
         }
         if (P.Ex2) {
-            const float2 e = P.Ex2[i];
+            const float2 e = k == tid ? e_pre : P.Ex2[i];
             const float dd = ff_f(ff_add(ex2, ff_neg(ff{e.x, e.y})));
-            b2 = dd * dd * P.inv_varx2[i];
+            b2 = dd * dd * (k == tid ? iv_pre : P.inv_varx2[i]);
         }
         float* co = P.cstat + (size_t)i * NCO;
+        if (fr_live) {
+            co[CO_MY] = ff_f(mean);
+            co[CO_MG] = nq == NQ ? ff_f(ff_mulf(s_q[2 * P.smax + k], iM)) : 0.0f;
+        }
         co[CO_VARY] = var_y;
         co[CO_VARX] = s2i * var_y;
         co[CO_DV] = dv;
@@ -140,38 +170,89 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
     }
     if (P.dfull_K > 0 && s_fr != nullptr && P.mode == 1 && H.phase == 0) {
         // App. B "Full rank": c_ik = Cov(y_i, s_k) with s_mk = g^m . z_k; the slice's
-        // coordinates receive sum_k (z_ki + c_ik)^2 (Hutchinson over the K vectors)
-        const int K = P.dfull_K;
-        const int nrow = ns * K + K;
-        for (int r = warp; r < nrow; r += nwarps) {
-            const size_t row = r < ns * K ? rows_fb(dp) + (size_t)(i0 + r / K) * K + (r % K)
-                                          : rows_fs(dp, K) + (size_t)(r - ns * K);
-            const float2* src = P.part + row * G;
-            ff s = ff_make(0.0f);
-            for (int c = lane; c < G; c += 32) {
-                const float2 v = __ldcg(src + c);
-                s = ff_add(s, ff{v.x, v.y});
-            }
-            s = group_sum_ff<32>(s);
-            if (lane == 0) s_fr[r] = s;
-        }
-        __syncthreads();
-        for (int kk = warp; kk < ns; kk += nwarps) {
+        // coordinates receive sum_k (z_ki + c_ik)^2 (Hutchinson over the K vectors).
+        // With the blocks' shifted records (y' = y - ybar', s' = s - gbar'.z, see
+        // fr_stride()):  M c_ik = sum_b Q_b,ik - (ybar_i - ybar'_i) sum_b S'_b,k.
+        // Thread (group gb, vector k) adds the blocks gb, gb + BG, ...; the BG
+        // partials are then added in group order.
+        const int K = P.dfull_K, K4 = fr_k4(K);
+        const size_t st = fr_stride(dp, K), oS = (size_t)dp * K4;
+        const float* FR = reinterpret_cast<const float*>(reinterpret_cast<const char*>(P.part) + fr_offset(dp, G));
+        const int KT = min(((K + 31) / 32) * 32, (int)blockDim.x), BG = (int)blockDim.x / KT;
+        const int kt = tid % KT, gb = tid / KT;
+#ifdef LAPS_PHASE_TIMING
+        unsigned long long frs_t_ = global_ns();
+#define FRS_MARK(k)                                                                   \
+    do {                                                                              \
+        __syncthreads();                                                              \
+        if (blockIdx.x == LAPS_PHASE_BLOCK && threadIdx.x == 0 && P.phase_ns) {       \
+            const unsigned long long now_ = global_ns();                              \
+            P.phase_ns[12 + (k)] += now_ - frs_t_;                                    \
+            frs_t_ = now_;                                                            \
+        }                                                                             \
+    } while (0)
+#else
+#define FRS_MARK(k) \
+    do {            \
+    } while (0)
+#endif
+        ff* s_part = s_fr;                                                   // [2][blockDim.x]
+        float* s_sq = s_old + P.smax;                                        // [ns][K]
+        const size_t step = (size_t)BG * st;
+        for (int kk = 0; kk < ns; ++kk) {
             const int i = i0 + kk;
-            // the difference E[y s] - ybar sbar is taken in binary64 (a few
-            // operations per coordinate and vector)
-            const double iMd = 1.0 / (double)P.M;
-            const double ybar = ff_to_double(s_q[kk]) * iMd;
-            float acc = 0.0f;
-            for (int k = lane; k < K; k += 32) {
-                const float z = rademacher((uint32_t)i, (uint32_t)k, (uint32_t)H.t, P.pid, P.seed_lo, P.seed_hi);
-                const double c = ff_to_double(s_fr[kk * K + k]) * iMd - ybar * (ff_to_double(s_fr[ns * K + k]) * iMd);
-                const float zc = (float)((double)z + c);
-                acc = fmaf(zc, zc, acc);
-            }
+            const float dyb = ff_f(ff_mulf(s_q[kk], iM)) - s_old[kk];
+            for (int k0 = 0; k0 < K; k0 += KT) {
+                const int k = k0 + kt;
+                ff vq = ff_make(0.0f), vs = vq;
+                if (gb < BG && k < K) {
+                    constexpr int U = 8;
+                    const float* Rq = FR + (size_t)gb * st + (size_t)i * K4 + k;
+                    const float* Rs = FR + (size_t)gb * st + oS + k;
+                    for (int c = gb; c < G; c += U * BG, Rq += U * step, Rs += U * step) {
+                        float lq[U], ls[U];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) P.cstat[(size_t)i * NCO + CO_DFULL] = acc;
+                        for (int u = 0; u < U; ++u) {
+                            const size_t o = c + u * BG < G ? u * step : 0;  // a valid block for the tail
+                            lq[u] = __ldcg(Rq + o);
+                            ls[u] = __ldcg(Rs + o);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (c + u * BG >= G) break;
+                            vq = ff_add(vq, lq[u]);
+                            vs = ff_add(vs, ls[u]);
+                        }
+                    }
+                }
+                FRS_MARK(0);
+                if (gb < BG) {
+                    s_part[gb * KT + kt] = vq;
+                    s_part[blockDim.x + gb * KT + kt] = vs;
+                }
+                __syncthreads();
+                if (tid < KT && k0 + tid < K) {
+                    ff A = s_part[tid], S = s_part[blockDim.x + tid];
+                    for (int q = 1; q < BG; ++q) {
+                        A = ff_add(A, s_part[q * KT + tid]);
+                        S = ff_add(S, s_part[blockDim.x + q * KT + tid]);
+                    }
+                    const float mc = ff_f(ff_add(A, ff_make(-dyb * ff_f(S))));
+                    const float z = rademacher((uint32_t)i, (uint32_t)(k0 + tid), (uint32_t)H.t, P.pid, P.seed_lo,
+                                               P.seed_hi);
+                    const float zc = z + mc * iM;
+                    s_sq[kk * K + k0 + tid] = zc * zc;
+                }
+                __syncthreads();
+                FRS_MARK(1);
+            }
+        }
+        for (int kk = warp; kk < ns; kk += nwarps) {
+            float a = 0.0f;
+            for (int k = lane; k < K; k += 32) a += s_sq[kk * K + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) P.cstat[(size_t)(i0 + kk) * NCO + CO_DFULL] = a;
         }
     }
 }

@@ -7,6 +7,10 @@
 
 #include "../../include/laps.h"
 
+#ifndef LAPS_PHASE_BLOCK
+#define LAPS_PHASE_BLOCK 0  // diagnostic builds: the block whose phases are timed
+#endif
+
 namespace laps {
 
 // Hyperparameters and phase machine of Alg. 1 (identical in every block).
@@ -29,7 +33,9 @@ enum : int { NQ = 4 };
 enum : int { CS_DSUM = 0, CS_DSQ, CS_NFIN, CS_NBAD, CS_ASUM, NCS };
 enum : int { NCSF = 6 };  // floats per chain slot in shared memory (Delta as hi, lo)
 // per-coordinate results of the slice owners: Var y, Var x, (1 - V)^2, delta, b^2
-enum : int { CO_VARY = 0, CO_VARX, CO_DV, CO_DEL, CO_B2, NCO = 6 };
+// (slot 5: the full-rank proxy's sum over k; 6, 7: ensemble means of y and g, kept
+// for the next iteration's full-rank block products)
+enum : int { CO_VARY = 0, CO_VARX, CO_DV, CO_DEL, CO_B2, NCO = 8 };
 enum : int { SL_VAR = 0, SL_DV, SL_MAXDEL, SL_B2SUM, SL_B2MAX, NSL };
 
 struct KParams {
@@ -46,7 +52,7 @@ struct KParams {
     const float* x0;    // init: [M][d] caller layout, or nullptr for Philox
     float x0_scale;
     // reduction and window state (global)
-    float2* part;             // [NQ * d_pad + NCS][G] per-block float-float sums
+    float2* part;             // [NQ * d_pad + NCS][G] per-block float-float sums (+ full-rank records)
     float* cstat;             // [d_pad][NCO] per-coordinate results of the slice owners
     float2* ctot;             // [NCS] chain totals (written by the last block)
     float2* ring;             // [T + 1][d_pad] window values E[x_i^2] (float-float)
@@ -87,14 +93,48 @@ struct KParams {
     int dfull_K;              // > 0: full-rank D~ over this many Rademacher vectors (else diagonal)
 };
 
-// per-coordinate result slot of the full-rank bias proxy: sum_k (z_ki + c_ik)^2
-enum : int { CO_DFULL = 5 };
-// rows of the per-block columns: NQ d_pad coordinate rows, NCS chain rows, then
-// (full rank) d_pad K rows of sum_m y_i s_mk and K rows of sum_m s_mk
+// per-coordinate result slot of the full-rank bias proxy: sum_k (z_ki + c_ik)^2,
+// and the ensemble means E[y_i], E[g_i] it centres the next iteration on
+enum : int { CO_DFULL = 5, CO_MY = 6, CO_MG = 7 };
+// rows of the per-block columns: NQ d_pad coordinate rows, NCS chain rows
 __host__ __device__ inline size_t rows_fb(int d_pad) { return (size_t)NQ * d_pad + NCS; }
-__host__ __device__ inline size_t rows_fs(int d_pad, int K) { return rows_fb(d_pad) + (size_t)d_pad * K; }
-__host__ __device__ inline size_t rows_total(int d_pad, int K) {
-    return K > 0 ? rows_fs(d_pad, K) + (size_t)K : rows_fb(d_pad);
+
+// The full-rank proxy's per-block records (K vectors) follow the rows, 16-byte
+// aligned: one record of fr_stride() floats per block b.  With the common shifts
+// ybar', gbar' (the previous iteration's ensemble means, the same in every block),
+// y' = y - ybar' and s'_k = (g - gbar') . z_k:
+//   [d_pad][K4]  Q_ik = sum_{m in b} y'_mi s'_mk
+//   [K4]         sum_{m in b} s'_mk
+__host__ __device__ inline int fr_k4(int K) { return (K + 3) & ~3; }
+__host__ __device__ inline size_t fr_stride(int d_pad, int K) {
+    const size_t K4 = (size_t)fr_k4(K);
+    return (size_t)d_pad * K4 + K4;
+}
+__host__ __device__ inline size_t fr_offset(int d_pad, int G) {  // bytes from the start of part
+    return ((rows_fb(d_pad) * (size_t)G * 8 + 15) / 16) * 16;
+}
+__host__ __device__ inline size_t part_bytes(int d_pad, int G, int K) {
+    return K > 0 ? fr_offset(d_pad, G) + (size_t)G * fr_stride(d_pad, K) * 4 : rows_fb(d_pad) * (size_t)G * 8;
+}
+// the block product s = G Z is split over this many ranges of coordinates when its
+// 4 x 4 output tiles alone would leave threads idle
+__host__ __device__ inline int fr_jsplit(int d_pad, int slots, int K, int threads) {
+    const int tiles = ((slots + 3) / 4) * (fr_k4(K) / 4);
+    int js = threads / (tiles > 0 ? tiles : 1);
+    js = js < 8 ? js : 8;
+    js = js < d_pad / 4 ? js : d_pad / 4;
+    return js > 1 ? js : 1;
+}
+// shared memory of the full-rank proxy (bytes, after the reduction's slice rows):
+// [smax K + 3 threads] float-float for the slice owners, 16 bytes of alignment,
+// y and g [slots][d_pad], s [slots][K4], the shifts ybar' and gbar' [d_pad] each,
+// Rademacher words [4 ceil(d_pad/128)][K4], partial products of s [jsplit - 1][slots][K4]
+__host__ __device__ inline size_t fullrank_smem(int d_pad, int slots, int smax, int K, int threads) {
+    if (K <= 0) return 0;
+    const size_t K4 = (size_t)fr_k4(K), nzw = (size_t)((d_pad + 127) / 128) * 4;
+    const size_t js = (size_t)fr_jsplit(d_pad, slots, K, threads);
+    return ((size_t)smax * K + 3 * (size_t)threads) * 8 + 16 +
+           4 * (2 * (size_t)slots * d_pad + js * (size_t)slots * K4 + 2 * (size_t)d_pad + nzw * K4);
 }
 
 // one launch of the streamed path's chain-update kernel: the maps it applies,

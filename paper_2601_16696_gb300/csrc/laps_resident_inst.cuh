@@ -1,6 +1,6 @@
 // laps_resident_inst.cuh -- instantiates the resident kernel for one target
 // (LAPS_INST_KIND) over the supported (lanes per chain, coordinates per lane)
-// shapes and defines its host-side launch / occupancy dispatchers.  Each
+// shapes, with and without the full-rank bias proxy, and defines its host-side launch / occupancy dispatchers.  Each
 // target lives in its own translation unit so the shapes compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
@@ -25,9 +25,11 @@ namespace laps {
 
 template <int KIND>
 struct ResidentDispatch {
-    static const void* fn(int lpc, int cpl) {
-#define LAPS_FN(L, C) \
-    if (lpc == L && cpl == C) return reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C>);
+    static const void* fn(int lpc, int cpl, bool fr) {
+#define LAPS_FN(L, C)                                                                         \
+    if (lpc == L && cpl == C)                                                                 \
+        return fr ? reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, true>)    \
+                  : reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, false>);
         LAPS_SHAPES(LAPS_FN)
 #undef LAPS_FN
         return nullptr;
@@ -37,9 +39,10 @@ struct ResidentDispatch {
 #define LAPS_CAT2(a, b) a##b
 #define LAPS_CAT(a, b) LAPS_CAT2(a, b)
 
-// returns the kernel symbol for (lpc, cpl), or nullptr if not built
-const void* LAPS_CAT(resident_kernel_, LAPS_INST_KIND)(int lpc, int cpl) {
-    return ResidentDispatch<LAPS_INST_KIND>::fn(lpc, cpl);
+// returns the kernel symbol for (lpc, cpl), with the full-rank proxy's block
+// products when fr, or nullptr if not built
+const void* LAPS_CAT(resident_kernel_, LAPS_INST_KIND)(int lpc, int cpl, bool fr) {
+    return ResidentDispatch<LAPS_INST_KIND>::fn(lpc, cpl, fr);
 }
 
 }  // namespace laps

@@ -25,13 +25,14 @@
 namespace laps {
 
 // ---------------------------------------------------------------- phase timing
-// Built only with -DLAPS_PHASE_TIMING (a diagnostic build): block 0 adds the
-// %globaltimer time spent between consecutive marks to P.phase_ns[k].
+// Built only with -DLAPS_PHASE_TIMING (a diagnostic build): block
+// LAPS_PHASE_BLOCK (default 0) adds the %globaltimer time spent between
+// consecutive marks to P.phase_ns[k].
 #ifdef LAPS_PHASE_TIMING
 #define LAPS_PHASE_MARK(k)                                                              \
     do {                                                                                \
         __syncthreads();                                                                \
-        if (blockIdx.x == 0 && threadIdx.x == 0 && P.phase_ns) {                        \
+        if (blockIdx.x == LAPS_PHASE_BLOCK && threadIdx.x == 0 && P.phase_ns) {         \
             const unsigned long long now_ = global_ns();                                \
             if ((k) > 0) P.phase_ns[(k) - 1] += now_ - phase_t_;                        \
             phase_t_ = now_;                                                            \
@@ -43,8 +44,187 @@ namespace laps {
     } while (0)
 #endif
 
+// ---------------------------------------------------------------- full-rank proxy
+// ±1 with the sign of bit `sh` of w (set: +1), as a float: the bit moved to the
+// sign position and flipped against -1.0f
+__device__ __forceinline__ float pm_one(uint32_t w, uint32_t sh) {
+    return __int_as_float(((w >> sh) << 31) ^ 0xBF800000u);
+}
+
+// App. B "Full rank", the block's share: with z_k the K Rademacher vectors of
+// step t and the common shifts ybar', gbar' (the ensemble means of the previous
+// iteration, read from the per-coordinate results), the block's records
+// Q_ik = sum_m y'_mi s'_mk and sum_m s'_mk of y' = y - ybar', s'_k = (g - gbar') . z_k
+// (see fr_stride()).  The slice owners add the blocks' records and correct
+// for the shift with the current means, so no product of uncentred values
+// enters a covariance.  Both products are register-tiled, four chains (or
+// coordinates) by four vectors per thread, on shared memory.
+// Step one, inlined: the chains' y and g into shared memory (padding as zeros).
+template <int LPC, int CPL>
+__device__ __forceinline__ void fullrank_stage(const KParams& P, const float (&y)[CPL], const float (&g)[CPL],
+                                               bool active, int slot, int gl, float* f_y, float* f_g) {
+    const int dp = P.d_pad;
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = gl + LPC * k;
+        if (j < P.nblk) {
+            float4 vy, vg;
+            float* py = &vy.x;
+            float* pg = &vg.x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const bool in = active && 4 * j + c < P.d;
+                py[c] = in ? y[4 * k + c] : 0.0f;
+                pg[c] = in ? g[4 * k + c] : 0.0f;
+            }
+            *reinterpret_cast<float4*>(f_y + (size_t)slot * dp + 4 * j) = vy;
+            *reinterpret_cast<float4*>(f_g + (size_t)slot * dp + 4 * j) = vg;
+        }
+    }
+}
+
+// Diagnostic build only: the timed block adds the time of the full-rank
+// sub-steps to P.phase_ns[8 + k].
+#ifdef LAPS_PHASE_TIMING
+#define FR_MARK(k)                                                    \
+    do {                                                              \
+        __syncthreads();                                              \
+        if (blockIdx.x == LAPS_PHASE_BLOCK && threadIdx.x == 0 && P.phase_ns) { \
+            const unsigned long long now_ = global_ns();              \
+            P.phase_ns[8 + (k)] += now_ - fr_t_;                      \
+            fr_t_ = now_;                                             \
+        }                                                             \
+    } while (0)
+#else
+#define FR_MARK(k) \
+    do {           \
+    } while (0)
+#endif
+
+// Step two, the products; all threads of the block call it after the staging.
+// Only the kernels built with the full-rank proxy contain it, so its register
+// tiles do not raise the pressure of the diagonal kernels' chain update.
+// my, mg: thread tid's coordinate of the shifts (tid < d; threads >= d_pad).
+__device__ __forceinline__ void fullrank_products(const KParams& P, const Hyper& H, int slots, int K, int K4,
+                                               int nzw, float my, float mg, float* f_y, float* f_g, float* f_s,
+                                               float* f_my, float* f_mg, uint32_t* f_z) {
+    const int tid = threadIdx.x, dp = P.d_pad, G = P.G, b = blockIdx.x;
+    const int nb = min(slots, P.M - b * slots);
+#ifdef LAPS_PHASE_TIMING
+    unsigned long long fr_t_ = global_ns();
+#endif
+    if (tid < dp) {
+        f_my[tid] = my;
+        f_mg[tid] = mg;
+    }
+    const int n128 = nzw / 4;
+    for (int w = tid; w < K * n128; w += blockDim.x) {
+        const int blk = w % n128, k = w / n128;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)k, (uint32_t)H.t, TAG_Z | (P.pid << 8)),
+                                      P.seed_lo, P.seed_hi);
+        f_z[(size_t)(4 * blk + 0) * K4 + k] = r.x;
+        f_z[(size_t)(4 * blk + 1) * K4 + k] = r.y;
+        f_z[(size_t)(4 * blk + 2) * K4 + k] = r.z;
+        f_z[(size_t)(4 * blk + 3) * K4 + k] = r.w;
+    }
+    if (K4 > K)
+        for (int w = tid; w < nzw * (K4 - K); w += blockDim.x)
+            f_z[(size_t)(w / (K4 - K)) * K4 + K + w % (K4 - K)] = 0u;
+    __syncthreads();
+    // centre the block's chains (padding coordinates stay zero, idle slots stay zero)
+    for (int o = tid; o < nb * dp; o += blockDim.x) {
+        const int i = o % dp;
+        f_y[o] -= f_my[i];
+        f_g[o] -= f_mg[i];
+    }
+    __syncthreads();
+    FR_MARK(0);
+    // s' = G' Z over the block's slots: z multiplies exactly (±1).  Task (js, tile)
+    // adds coordinate blocks [js nblk / JS, (js + 1) nblk / JS) into buffer js.
+    const int ntk = K4 / 4, nts = (slots + 3) / 4, ntile = nts * ntk;
+    const int JS = fr_jsplit(dp, slots, K, blockDim.x);
+    float* f_sp = reinterpret_cast<float*>(f_z + (size_t)nzw * K4);  // [JS - 1][slots][K4]
+    for (int task = tid; task < JS * ntile; task += blockDim.x) {
+        const int js = task / ntile, tile = task - js * ntile;
+        const int s0 = 4 * (tile / ntk), k0 = 4 * (tile - (tile / ntk) * ntk);
+        const int j0 = (js * P.nblk) / JS, j1 = ((js + 1) * P.nblk) / JS;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+        for (int j = j0; j < j1; ++j) {
+            const uint4 w = *reinterpret_cast<const uint4*>(f_z + (size_t)(j >> 3) * K4 + k0);
+            float4 gv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                gv[a] = s0 + a < slots ? *reinterpret_cast<const float4*>(f_g + (size_t)(s0 + a) * dp + 4 * j)
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t sh = (uint32_t)((4 * j + c) & 31);
+                const float z[4] = {pm_one(w.x, sh), pm_one(w.y, sh), pm_one(w.z, sh), pm_one(w.w, sh)};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float gc = c == 0 ? gv[a].x : c == 1 ? gv[a].y : c == 2 ? gv[a].z : gv[a].w;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(gc, z[q], acc[a][q]);
+                }
+            }
+        }
+        float* dst = js == 0 ? f_s : f_sp + (size_t)(js - 1) * slots * K4;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            if (s0 + a < slots)
+                *reinterpret_cast<float4*>(dst + (size_t)(s0 + a) * K4 + k0) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    }
+    if (JS > 1) {
+        __syncthreads();
+        for (int o = tid; o < slots * K4; o += blockDim.x) {
+            float v = f_s[o];
+            for (int js = 1; js < JS; ++js) v += f_sp[(size_t)(js - 1) * slots * K4 + o];
+            f_s[o] = v;
+        }
+    }
+    __syncthreads();
+    FR_MARK(1);
+    float* R = reinterpret_cast<float*>(reinterpret_cast<char*>(P.part) + fr_offset(dp, G)) +
+               (size_t)b * fr_stride(dp, K);
+    for (int k = tid; k < K4; k += blockDim.x) {
+        float ss = 0.0f;
+        for (int sl = 0; sl < nb; ++sl) ss += f_s[(size_t)sl * K4 + k];
+        R[(size_t)dp * K4 + k] = ss;
+    }
+    FR_MARK(2);
+    // Q = Y'^T S' over the block's chains, rows of K4 floats (coalesced float4 stores)
+    const int nti = (P.d + 3) / 4;
+    for (int tile = tid; tile < nti * ntk; tile += blockDim.x) {
+        const int i0 = 4 * (tile / ntk), k0 = 4 * (tile - (tile / ntk) * ntk);
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+        for (int sl = 0; sl < nb; ++sl) {
+            const float4 yv = *reinterpret_cast<const float4*>(f_y + (size_t)sl * dp + i0);
+            const float4 sv = *reinterpret_cast<const float4*>(f_s + (size_t)sl * K4 + k0);
+            const float ya[4] = {yv.x, yv.y, yv.z, yv.w}, sa[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(ya[a], sa[q], acc[a][q]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            *reinterpret_cast<float4*>(R + (size_t)(i0 + a) * K4 + k0) =
+                make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    }
+    FR_MARK(3);
+}
+
 // ---------------------------------------------------------------- the kernel
-template <int KIND, int LPC, int CPL>
+template <int KIND, int LPC, int CPL, bool FR>
 __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParams P,
                                                                    const Coefs* __restrict__ coefs) {
     constexpr int NB = CPL / 4;
@@ -69,13 +249,17 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     float* s_cs = sq + (size_t)P.qpp * nwarps * dp;                   // [slots][NCSF]
     float* s_var = s_cs + (size_t)slots * NCSF;                       // [dp] Var y (switch)
     ff* s_q = reinterpret_cast<ff*>(s_var + dp);                      // [NQ][smax] + [NCS]
-    // full-rank bias proxy only (App. B "Full rank", K Rademacher vectors)
-    const int KF = P.dfull_K, nb128 = (dp + 127) / 128;
-    ff* s_fr = s_q + (size_t)NQ * P.smax + NCS;                       // [smax K + K]
-    float* f_y = reinterpret_cast<float*>(s_fr + (size_t)P.smax * KF + KF);  // [slots][dp]
-    float* f_g = f_y + (size_t)slots * dp;                            // [slots][dp]
-    float* f_s = f_g + (size_t)slots * dp;                            // [slots][K]
-    uint32_t* f_z = reinterpret_cast<uint32_t*>(f_s + (size_t)slots * KF);  // [K][nb128][4]
+    // full-rank bias proxy only (App. B "Full rank", K Rademacher vectors); the
+    // layout is the one fullrank_smem() sizes
+    const int KF = FR ? P.dfull_K : 0, K4 = (KF + 3) & ~3, nzw = ((dp + 127) / 128) * 4;
+    ff* s_fr = s_q + (size_t)NQ * P.smax + NCS;  // [3 threads] + [smax K]: the slice owners' partials
+    float* f_y = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(s_fr + (size_t)P.smax * KF + 3 * blockDim.x) + 15) & ~(uintptr_t)15);  // [slots][dp]
+    float* f_g = f_y + (size_t)slots * dp;                   // [slots][dp]
+    float* f_s = f_g + (size_t)slots * dp;                   // [slots][K4]
+    float* f_my = f_s + (size_t)slots * K4;                  // [dp] shift ybar'
+    float* f_mg = f_my + dp;                                 // [dp] shift gbar'
+    uint32_t* f_z = reinterpret_cast<uint32_t*>(f_mg + dp);  // [nzw][K4] Rademacher words
 
     if (tid == 0) {
         H = *P.hyper;
@@ -160,6 +344,13 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     for (int it = 0; it < n_iter; ++it) {
         if (P.mode == 1 && H.done) break;
         LAPS_PHASE_MARK(0);
+        // full-rank proxy: the previous iteration's means (the block products' shift),
+        // loaded now so that their latency hides behind the chain update
+        float fr_my = 0.0f, fr_mg = 0.0f;
+        if (FR && KF > 0 && P.mode == 1 && H.phase == 0 && tid < P.d) {
+            fr_my = __ldcg(P.cstat + (size_t)tid * NCO + CO_MY);
+            fr_mg = __ldcg(P.cstat + (size_t)tid * NCO + CO_MG);
+        }
         // ------------------------------------------------ 1. chain update
         ff c_d = ff_make(0.0f);
         float c_d2 = 0.0f, c_fin = 0.0f, c_bad = 0.0f, c_a = 0.0f;
@@ -282,57 +473,9 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             s = group_sum_ff<32>(s);
             if (lane == 0) P.part[((size_t)NQ * dp + k) * G + blockIdx.x] = make_float2(s.hi, s.lo);
         }
-        if (KF > 0 && P.mode == 1 && H.phase == 0) {
-            // App. B "Full rank": this block's sum_m y_i s_mk and sum_m s_mk with
-            // s_mk = g^m . z_k, as two small block products on shared memory
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const int j = gl + LPC * k;
-                if (j < P.nblk)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        f_y[(size_t)slot * dp + 4 * j + c] = active ? y[4 * k + c] : 0.0f;
-                        f_g[(size_t)slot * dp + 4 * j + c] = active ? g[4 * k + c] : 0.0f;
-                    }
-            }
-            for (int w = tid; w < KF * nb128; w += blockDim.x) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)(w % nb128), (uint32_t)(w / nb128),
-                                                         (uint32_t)H.t, TAG_Z | (P.pid << 8)),
-                                              P.seed_lo, P.seed_hi);
-                uint32_t* zw = f_z + (size_t)w * 4;
-                zw[0] = r.x; zw[1] = r.y; zw[2] = r.z; zw[3] = r.w;
-            }
-            __syncthreads();
-            for (int o = tid; o < slots * KF; o += blockDim.x) {
-                const int sl = o / KF, k = o - sl * KF;
-                const float* gs = f_g + (size_t)sl * dp;
-                const uint32_t* zk = f_z + (size_t)k * nb128 * 4;
-                float acc = 0.0f;
-                for (int i = 0; i < P.d; ++i) {
-                    const bool plus = (zk[i >> 5] >> (i & 31)) & 1u;
-                    acc += plus ? gs[i] : -gs[i];
-                }
-                f_s[o] = acc;
-            }
-            __syncthreads();
-            const size_t rb = rows_fb(dp), rs = rows_fs(dp, KF);
-            // exact products (fma residual) summed in float-float: the covariance
-            // is a small difference of E[y s] and ybar sbar
-            for (int o = tid; o < P.d * KF; o += blockDim.x) {
-                const int i = o / KF, k = o - i * KF;
-                ff acc = ff_make(0.0f);
-                for (int sl = 0; sl < slots; ++sl) {
-                    const float a = f_y[(size_t)sl * dp + i], b = f_s[(size_t)sl * KF + k];
-                    const float p = a * b;
-                    acc = ff_add(acc, ff{p, fmaf(a, b, -p)});
-                }
-                P.part[(rb + (size_t)i * KF + k) * G + blockIdx.x] = make_float2(acc.hi, acc.lo);
-            }
-            for (int k = tid; k < KF; k += blockDim.x) {
-                ff acc = ff_make(0.0f);
-                for (int sl = 0; sl < slots; ++sl) acc = ff_add(acc, f_s[(size_t)sl * KF + k]);
-                P.part[(rs + k) * G + blockIdx.x] = make_float2(acc.hi, acc.lo);
-            }
+        if (FR && KF > 0 && P.mode == 1 && H.phase == 0) {
+            fullrank_stage<LPC, CPL>(P, y, g, active, slot, gl, f_y, f_g);
+            fullrank_products(P, H, slots, KF, K4, nzw, fr_my, fr_mg, f_y, f_g, f_s, f_my, f_mg, f_z);
         }
         LAPS_PHASE_MARK(3);
         // ------------------------------------------------ 3. barrier, then this block's slice
@@ -340,7 +483,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         if (!grid_sync_count(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns))
             return;
         LAPS_PHASE_MARK(4);
-        ens_slice(P, H, s_q, blockIdx.x, G, KF > 0 ? s_fr : nullptr);
+        ens_slice(P, H, s_q, blockIdx.x, G, FR ? s_fr : nullptr);
         LAPS_PHASE_MARK(5);
         // ------------------------------------------------ 4. barrier, then every block gathers
         n_bar += 1;
