@@ -53,7 +53,11 @@ typedef enum {
     LAPS_GAUSS_DIAG = 0,  /* log p = -1/2 sum_i prec_i x_i^2 */
     LAPS_BANANA = 1,      /* pairs (a,b) = (x_2k, x_2k+1): a ~ N(0,1), b|a ~ N(a^2, sb^2); d even */
     LAPS_FUNNEL = 2,      /* v = x_0 ~ N(0, sv^2), x_i|v ~ N(0, e^v), i = 1..d-1 */
-    LAPS_LOGREG = 3       /* sum_n [y_n z_n - softplus(z_n)] - |w|^2/(2 prior_var), z = X w */
+    LAPS_LOGREG = 3,      /* sum_n [y_n z_n - softplus(z_n)] - |w|^2/(2 prior_var), z = X w */
+    LAPS_GAUSS_DENSE = 4  /* -1/2 x^T P x with a dense symmetric positive-definite precision P
+                             (Sec. 6, the randomly oriented ill-conditioned Gaussian); d <= 512;
+                             sampled on the streamed path, its gradient -P x as one
+                             chains-by-coordinates contraction per step */
 } laps_target_kind;
 
 /* Arithmetic of the logistic-regression contraction in the unadjusted phase. */
@@ -65,7 +69,9 @@ typedef enum {
 typedef struct {
     laps_target_kind kind;
     int64_t d;              /* dimension, >= 2 */
-    const float* prec;      /* GAUSS_DIAG: device [d] precisions 1/sigma_i^2 */
+    const float* prec;      /* GAUSS_DIAG: device [d] precisions 1/sigma_i^2;
+                               GAUSS_DENSE: device [d][d] precision matrix, row-major, symmetric
+                               (the target keeps its own zero-padded copy) */
     double banana_sb;       /* BANANA: conditional std of x_b (0.1) */
     double funnel_sv;       /* FUNNEL: std of v (3) */
     int64_t n_data;         /* LOGREG: rows of X */

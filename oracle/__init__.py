@@ -22,7 +22,7 @@ _SO = os.path.join(_HERE, "liblaps_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-GAUSS_DIAG, BANANA, FUNNEL, LOGREG = 0, 1, 2, 3
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE = 0, 1, 2, 3, 4
 LF, MN2, MN4 = 0, 1, 2
 TAG_X0, TAG_O1, TAG_O2, TAG_REFRESH, TAG_MH = 0, 1, 2, 3, 4
 

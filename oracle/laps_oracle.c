@@ -110,6 +110,14 @@ double ora_logp_grad(const ora_target* tg, const double* x, double* g) {
             g[i] = -tg->prec[i] * x[i];
         }
         break;
+    case ORA_GAUSS_DENSE: /* -1/2 x^T P x, grad -P x (Sec. 6, the rotated ill-conditioned Gaussian) */
+        for (int64_t i = 0; i < d; ++i) {
+            double r = 0.0;
+            for (int64_t j = 0; j < d; ++j) r += tg->prec[i * d + j] * x[j];
+            g[i] = -r;
+            lp += -0.5 * x[i] * r;
+        }
+        break;
     case ORA_BANANA: { /* pairs (a, b) = (x_2k, x_2k+1): a ~ N(0,1), b|a ~ N(a^2, s^2) */
         const double s2 = tg->banana_sb * tg->banana_sb;
         for (int64_t k = 0; 2 * k + 1 < d; ++k) {

@@ -36,11 +36,12 @@ void ora_normals(uint64_t seed, uint32_t m, uint32_t t, uint32_t tag, uint32_t p
                  int64_t d, double* z);
 
 /* ---- targets ---- */
-enum { ORA_GAUSS_DIAG = 0, ORA_BANANA = 1, ORA_FUNNEL = 2, ORA_LOGREG = 3 };
+enum { ORA_GAUSS_DIAG = 0, ORA_BANANA = 1, ORA_FUNNEL = 2, ORA_LOGREG = 3, ORA_GAUSS_DENSE = 4 };
 typedef struct {
     int kind;
     int64_t d;
-    const double* prec;      /* GAUSS_DIAG: precision 1/sigma_i^2, [d] */
+    const double* prec;      /* GAUSS_DIAG: precision 1/sigma_i^2, [d];
+                                GAUSS_DENSE: precision matrix P, row-major [d][d] (symmetric) */
     double banana_sb;        /* BANANA: std of x_b given x_a (0.1) */
     double funnel_sv;        /* FUNNEL: std of v (3) */
     int64_t n_data;          /* LOGREG: number of data rows */

@@ -321,6 +321,12 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
         if ((d + 63) / 64 * 64 > kLogregMaxKp)
             return fail(LAPS_ERR_UNSUPPORTED, "LOGREG is built for d <= " + std::to_string(kLogregMaxKp));
         break;
+    case LAPS_GAUSS_DENSE:
+        if (!desc->prec || !aligned(desc->prec, 4))
+            return fail(LAPS_ERR_INVALID_ARG, "GAUSS_DENSE needs a device prec[d][d]");
+        if (d > kDenseMaxDim)
+            return fail(LAPS_ERR_UNSUPPORTED, "GAUSS_DENSE is built for d <= " + std::to_string(kDenseMaxDim));
+        break;
     default:
         return fail(LAPS_ERR_INVALID_ARG, "unknown target kind");
     }
@@ -335,6 +341,20 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
         cudaMemset(t->prec_pad, 0, t->d_pad * sizeof(float));
         e = cudaMemcpy(t->prec_pad, desc->prec, d * sizeof(float), cudaMemcpyDeviceToDevice);
         if (e != cudaSuccess) { cudaFree(t->prec_pad); delete t; return cuda_fail(e, "copy prec"); }
+    }
+    if (desc->kind == LAPS_GAUSS_DENSE) {
+        // padded to whole 32-column tiles of the contraction; padding rows and columns are zero
+        t->d_pad = (int)((d + 31) / 32 * 32);
+        const size_t pb = (size_t)t->d_pad * t->d_pad * sizeof(float);
+        cudaError_t e = cudaMalloc(&t->prec_dense, pb);
+        if (e == cudaSuccess) e = cudaMemset(t->prec_dense, 0, pb);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(t->prec_dense, t->d_pad * sizeof(float), desc->prec, d * sizeof(float),
+                             d * sizeof(float), d, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            laps_target_destroy(t);
+            return cuda_fail(e, "GAUSS_DENSE precision copy");
+        }
     }
     if (desc->kind == LAPS_LOGREG) {
         // padded row stride: a multiple of 64 features for the contraction kernels
@@ -378,6 +398,7 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
 void laps_target_destroy(laps_target* t) {
     if (!t) return;
     if (t->prec_pad) cudaFree(t->prec_pad);
+    if (t->prec_dense) cudaFree(t->prec_dense);
     if (t->lr.X) cudaFree(t->lr.X);
     if (t->lr.y) cudaFree(t->lr.y);
     if (t->lr.Xb) cudaFree(t->lr.Xb);
@@ -394,7 +415,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
         !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0 || cfg->dtilde_K < 0 ||
         cfg->dtilde_K > 1024)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
-    if (cfg->dtilde_K > 0 && tg->kind == TGT_LOGREG)
+    if (cfg->dtilde_K > 0 && streamed_kind(tg->kind))
         return fail(LAPS_ERR_UNSUPPORTED, "the full-rank bias proxy is built for the register-resident targets");
     laps_ctx* c = new laps_ctx();
     c->tg = tg;
@@ -404,7 +425,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     c->d_pad = tg->d_pad;
     c->T = std::max(2, (int)std::ceil(cfg->window_frac * (double)cfg->n_total_steps));
     c->trace_cap = cfg->n_total_steps + 2;
-    laps_status st = tg->kind == TGT_LOGREG ? streamed_setup(c) : choose_shape(c);
+    laps_status st = streamed_kind(tg->kind) ? streamed_setup(c) : choose_shape(c);
     if (st != LAPS_OK) { delete c; return st; }
     const size_t Md = (size_t)M * c->d_pad;
     auto alloc = [&](void** p, size_t bytes) -> bool {

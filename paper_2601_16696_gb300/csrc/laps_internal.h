@@ -14,6 +14,7 @@ struct laps_target {
     int kind = 0, d = 0, d_pad = 0;
     float* prec_pad = nullptr;  // GAUSS_DIAG precisions, zero padded to d_pad (owned)
     laps::LogregData lr{};      // LOGREG: padded copies of X and y (owned)
+    float* prec_dense = nullptr; // GAUSS_DENSE: P [d_pad][d_pad], zero padded, d_pad = 32 k (owned)
     int* status = nullptr;      // LOGREG: latched status of the tensor-core target call (owned)
 };
 
@@ -90,6 +91,11 @@ laps_status streamed_setup(laps_ctx* c);
 laps_status streamed_alloc(laps_ctx* c);
 laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st);
 laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st);
+// dense-precision Gaussian (laps_gauss_dense.cu): G = -W P, LP = -1/2 sum W (P W)
+constexpr int kDenseMaxDim = 512;
+cudaError_t gauss_dense_grad(const float* P, int d_pad, int d, const float* W, int64_t M, float* G,
+                             float2* LP, cudaStream_t st);
+inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_GAUSS_DENSE; }
 laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
                                  float2* lpart, cudaStream_t st);
 laps_status status_error(int device_status);

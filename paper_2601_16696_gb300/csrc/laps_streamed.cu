@@ -405,6 +405,10 @@ laps_status launch_seg(laps_ctx* c, const KParams& P, const SegOp& op, cudaStrea
 // precision, unadjusted phase), else FP32
 laps_status launch_grad(laps_ctx* c, bool mma, cudaStream_t st) {
     cudaError_t e;
+    if (c->tg->kind == TGT_GAUSS_DENSE) {
+        e = gauss_dense_grad(c->tg->prec_dense, c->d_pad, c->d, c->W, c->M, c->gpart, c->lpart, st);
+        return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
+    }
     if (mma)
         e = logreg_grad_mma(c->tg->lr, c->tmW, c->W, c->M, c->nsplit_mma, c->rps_mma, c->gpart, c->lpart,
                             c->status, c->cfg.barrier_timeout_ns, st);
@@ -503,7 +507,7 @@ laps_status read_hyper(laps_ctx* c, cudaStream_t st, Hyper& h) {
 
 laps_status streamed_setup(laps_ctx* c) {
     const int dp = c->d_pad;
-    if (c->tg->kind != TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "streamed path: LOGREG only");
+    if (!streamed_kind(c->tg->kind)) return fail(LAPS_ERR_UNSUPPORTED, "streamed path: LOGREG and GAUSS_DENSE only");
     c->streamed = true;
     c->seg_cpl = dp <= 128 ? 4 : dp <= 256 ? 8 : dp <= 512 ? 16 : 0;
     if (c->seg_cpl == 0) return fail(LAPS_ERR_UNSUPPORTED, "streamed path: d_pad > 512");
@@ -526,6 +530,7 @@ laps_status streamed_setup(laps_ctx* c) {
     // data splits of the gradient: about two blocks of 64 chains per SM
     const int64_t tiles = (c->M + 63) / 64;
     c->nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * nsm + tiles - 1) / tiles));
+    if (c->tg->kind == TGT_GAUSS_DENSE) c->nsplit = 1;  // one block holds every coordinate of its chains
     c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
     coefs_table(c->cf);
     if (c->cfg.precision == LAPS_MIXED) {
@@ -638,6 +643,10 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
 
 laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
                                  float2* lpart, cudaStream_t st) {
+    if (tg->kind == TGT_GAUSS_DENSE) {
+        cudaError_t e = gauss_dense_grad(tg->prec_dense, tg->d_pad, tg->d, W, M, gpart, lpart, st);
+        return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
+    }
     cudaError_t e = logreg_grad_f32(tg->lr, W, M, 1, gpart, lpart, st);
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logreg gradient");
 }

@@ -95,9 +95,11 @@ __global__ void logreg_unpack_kernel(const float* __restrict__ G, const float2* 
     }
 }
 
-static laps_status logreg_logp_grad(const laps_target* tg, const float* x, int64_t M, float* logp,
-                                    float* grad, cudaStream_t st) {
-    const int kp = tg->lr.kp, d = tg->d;
+// targets evaluated by an ensemble contraction (LOGREG, GAUSS_DENSE): the points
+// packed to the contraction's padded rows, its partials back to [M][d]
+static laps_status streamed_logp_grad(const laps_target* tg, const float* x, int64_t M, float* logp,
+                                      float* grad, cudaStream_t st) {
+    const int kp = tg->d_pad, d = tg->d;
     float *W = nullptr, *G = nullptr;
     float2* lp = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&W, (size_t)M * kp * 4, st);
@@ -117,7 +119,7 @@ static laps_status logreg_logp_grad(const laps_target* tg, const float* x, int64
     if (G) cudaFreeAsync(G, st);
     if (lp) cudaFreeAsync(lp, st);
     if (rs != LAPS_OK) return rs;
-    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "LOGREG logp_grad");
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logp_grad of a contraction target");
 }
 
 // LOGREG on the tensor cores (the mixed-precision form's unadjusted-phase
@@ -190,7 +192,7 @@ extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float*
                                              float* logp, float* grad, void* stream) {
     if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (M == 0) return LAPS_OK;
-    if (tg->kind == TGT_LOGREG) return logreg_logp_grad(tg, x, M, logp, grad, (cudaStream_t)stream);
+    if (streamed_kind(tg->kind)) return streamed_logp_grad(tg, x, M, logp, grad, (cudaStream_t)stream);
     const int threads = 256;
     const int64_t blocks = (M * 32 + threads - 1) / threads;
     if (blocks > 0x7fffffff) return fail(LAPS_ERR_INVALID_ARG, "M too large");

@@ -18,7 +18,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblaps.so")
 
-GAUSS_DIAG, BANANA, FUNNEL, LOGREG = 0, 1, 2, 3
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE = 0, 1, 2, 3, 4
 FP32, MIXED = 0, 1
 LF, MN2, MN4 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NONFINITE",

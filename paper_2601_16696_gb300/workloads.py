@@ -19,6 +19,11 @@ for them with the same shapes and structure:
                    100 standardised N(0,1) columns plus an intercept), w_true ~
                    N(0, I/100), y ~ Bernoulli(sigmoid(X w_true)), prior N(0, I),
                    M = 8192;
+* ``icg_d100``     ill-conditioned Gaussian, d = 100: covariance R diag(lam) R^T
+                   with lam ~ Gamma(1/2, 1) (condition number 1.1e5 at seed 0)
+                   and R a random rotation (QR of a Gaussian matrix); the
+                   target is given by its precision matrix, M = 4096,
+                   x0 ~ N(0, I), 2000 steps;
 * ``batch64``      64 diagonal Gaussians, d log-uniform in [10, 2000],
                    condition number log-uniform in [1e2, 1e4], chains from
                    {512, 1024, 2048, 4096}, plus one d = 10000 Gaussian with
@@ -30,7 +35,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-GAUSS_DIAG, BANANA, FUNNEL, LOGREG = 0, 1, 2, 3
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -41,7 +46,7 @@ class Problem:
     M: int
     n_steps: int
     x0: np.ndarray                    # [M, d] float32-representable float64
-    prec: np.ndarray | None = None    # GAUSS_DIAG precisions [d]
+    prec: np.ndarray | None = None    # GAUSS_DIAG precisions [d]; GAUSS_DENSE precision matrix [d, d]
     banana_sb: float = 0.1
     funnel_sv: float = 3.0
     X: np.ndarray | None = None       # LOGREG design [N, d]
@@ -95,6 +100,25 @@ def funnel(d: int = 101, M: int = 4096, n_steps: int = 5000, sv: float = 3.0,
     ex2[0], vx2[0] = s2, 2.0 * s2 * s2
     return Problem("funnel_d%d" % d, FUNNEL, d, M, n_steps, x0, funnel_sv=sv, Ex2=ex2,
                    Varx2=vx2, seed=seed)
+
+
+def icg(d: int = 100, M: int = 4096, n_steps: int = 2000, shape: float = 0.5, seed: int = 0,
+        x0_scale: float = 1.0) -> Problem:
+    """Randomly oriented Gaussian with eigenvalues of the covariance drawn from
+    Gamma(shape, 1).  The precision matrix P = R diag(1/lam) R^T is rounded to
+    binary32 (the target both implementations receive); the truths come from
+    the covariance inv(P) of that rounded matrix, in binary64."""
+    rng = np.random.default_rng(seed)
+    lam = rng.gamma(shape, 1.0, d)
+    R, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    P = (R / lam) @ R.T
+    prec = _f32(0.5 * (P + P.T))
+    cov = np.linalg.inv(prec)
+    ex2 = np.diag(cov).copy()
+    x0 = _f32(x0_scale * rng.standard_normal((M, d)))
+    return Problem("icg_d%d" % d, GAUSS_DENSE, d, M, n_steps, x0, prec=prec, Ex2=ex2,
+                   Varx2=2.0 * ex2 * ex2, seed=seed,
+                   extra={"cond": float(lam.max() / lam.min()), "cov": cov})
 
 
 def logreg(n_data: int = 10000, n_feat: int = 100, M: int = 8192, n_steps: int = 2000,
@@ -173,5 +197,5 @@ def batch64(seed: int = 0, n_small: int = 64, big_d: int = 10000, big_M: int = 1
 
 def by_name(name: str, **kw) -> Problem:
     table = {"gauss_d100": gauss_diag, "banana_d100": banana, "funnel_d101": funnel,
-             "logreg_d101": logreg}
+             "logreg_d101": logreg, "icg_d100": icg}
     return table[name](**kw)

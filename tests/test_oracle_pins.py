@@ -90,7 +90,13 @@ def _targets(ora):
         ora.OracleTarget(ora.BANANA, 6, banana_sb=0.1),
         ora.OracleTarget(ora.FUNNEL, 5, funnel_sv=3.0),
         ora.OracleTarget(ora.LOGREG, 4, X=X, y=y, prior_var=1.0),
+        ora.OracleTarget(ora.GAUSS_DENSE, 5, prec=_spd(rng, 5)),
     ]
+
+
+def _spd(rng, d):
+    A = rng.standard_normal((d, d))
+    return A @ A.T / d + 0.1 * np.eye(d)
 
 
 def test_gradients_central_differences(ora):
@@ -146,6 +152,46 @@ def test_funnel_score_identities_exact_samples(ora):
     v = sv * rng.standard_normal(M)
     x = rng.standard_normal((M, 3)) * np.exp(v / 2)[:, None]
     _score_identities(ora.OracleTarget(ora.FUNNEL, 4, funnel_sv=sv), np.column_stack([v, x]))
+
+
+def test_dense_gauss_score_identities_exact_samples(ora):
+    """Exact draws of the rotated ill-conditioned Gaussian (the workload's own
+    precision matrix, d = 100): E[grad log p] = 0 and Cov(x, grad log p) = -I,
+    the whole matrix (a dropped or misplaced entry of P x shows off the
+    diagonal); and log p's value at x = P^-1 b is -1/2 b^T P^-1 b."""
+    pr = W.icg(d=100, M=8)
+    tg = ora.OracleTarget(ora.GAUSS_DENSE, pr.d, prec=pr.prec)
+    rng = np.random.default_rng(7)
+    Lc = np.linalg.cholesky(pr.extra["cov"])
+    M = 20000
+    X = rng.standard_normal((M, pr.d)) @ Lc.T
+    _, G = tg.logp_grad(X)
+    # normalise each coordinate pair by its natural scale sqrt(E x_i^2 E g_j^2)
+    sx = np.sqrt(np.mean(X * X, axis=0))
+    sg = np.sqrt(np.mean(G * G, axis=0))
+    np.testing.assert_allclose(G.mean(axis=0) / sg, 0.0, atol=5.0 / np.sqrt(M))
+    V = (X - X.mean(0)).T @ (G - G.mean(0)) / M
+    np.testing.assert_allclose(V / np.outer(sx, sg), -np.eye(pr.d) / np.outer(sx, sg),
+                               atol=6.0 / np.sqrt(M))
+    b = rng.standard_normal(pr.d)
+    x = np.linalg.solve(pr.prec, b)
+    lp, g = tg.logp_grad(x)
+    np.testing.assert_allclose(g, -b, rtol=1e-8, atol=1e-8)
+    assert lp == pytest.approx(-0.5 * b @ x, rel=1e-10)
+
+
+def test_icg_workload_condition_and_truth():
+    """The stand-in for the paper's ill-conditioned Gaussian: d = 100, condition
+    number about 1e5, a dense rotation (every precision row has many
+    non-negligible entries), and truths from the covariance of the rounded P."""
+    pr = W.icg()
+    ev = np.linalg.eigvalsh(pr.prec)
+    assert 5e4 < ev.max() / ev.min() < 2e5
+    off = np.abs(pr.prec - np.diag(np.diag(pr.prec)))
+    assert (off > 1e-3 * np.abs(pr.prec).max()).sum(axis=1).min() > 50
+    np.testing.assert_allclose(pr.Ex2, np.diag(np.linalg.inv(pr.prec)), rtol=1e-9)
+    assert np.array_equal(pr.prec, pr.prec.T)
+    assert np.array_equal(pr.prec, pr.prec.astype(np.float32).astype(np.float64))
 
 
 def test_gauss_truth_moments_match_workload():
