@@ -174,10 +174,12 @@ def _forms(flush, stream, mhz, seed0):
     """The other forms of the path, measured in the same run and reported
     beside the headline: the logistic regression (d = 101 with intercept,
     n = 10^4 rows, M = 8192) with the BF16 tensor-core contraction in the
-    unadjusted phase beside the all-FP32 form, and the batch of 64 uneven
-    diagonal Gaussians plus one d = 10^4, M = 16384 problem in one persistent
-    launch.  Each: chain-gradient evaluations per second of a whole run, wall
-    time to b^2 < 0.01, and the dominant kernel against its roofline."""
+    unadjusted phase beside the all-FP32 form; the batch of 64 uneven diagonal
+    Gaussians plus one d = 10^4, M = 16384 problem in one persistent launch; the
+    rotated ill-conditioned Gaussian (d = 100, M = 4096, dense precision).
+    Each: chain-gradient evaluations per second of a whole run, wall time to
+    b^2 < 0.01, and the dominant kernel against its roofline.  Also the cost of
+    an unadjusted iteration with the full-rank bias proxy (K = 20, 100)."""
     import torch
     from paper_2601_16696_gb300 import laps, workloads
     pk = _peaks()
@@ -267,6 +269,46 @@ def _forms(flush, stream, mhz, seed0):
                      "basis": "16 B per coordinate-step (y, u read and written), %.3f ms per "
                               "unadjusted iteration of the whole batch" % it_ms},
     }
+    # ---- the rotated ill-conditioned Gaussian (dense precision, streamed path)
+    pr = workloads.icg()
+    tg = laps.Target.from_problem(pr)
+    x0 = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        tg.logp_grad(x0)
+    reps = 20
+    gms = timed_ms(lambda: [tg.logp_grad(x0) for _ in range(reps)]) / reps
+    s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, stop_b2_max=1)  # b2_first on b^2_max
+    s.set_truth(pr.Ex2, pr.Varx2)
+    s.init(x0, seed=seed0)
+    s.step(3)
+    run_ms = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
+    st = s.stats()
+    flops = 2.0 * pr.M * pr.d * pr.d  # the contraction -P x of every chain, per gradient
+    achieved = flops / (gms * 1e-3) / 1e12
+    out["icg"] = {
+        "workload": "icg_d%d_M%d_%dsteps (cond %.2g)" % (pr.d, pr.M, pr.n_steps, pr.extra["cond"]),
+        "value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT, "run_ms": run_ms,
+        "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
+        "time_to_b2_ms": st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None,
+        "grads_to_b2": st["b2_first_grads"] if st["b2_first_t"] >= 0 else None, "b2": "b2_max",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "gauss_dense_grad_kernel<4,4>",
+                     "timed": "laps_target_logp_grad (points packed, contraction, partials "
+                              "unpacked), %.3f ms per call; 2 M d^2 algorithmic FLOP, the "
+                              "compensated accumulation's extra operations not counted" % gms,
+                     "peak_basis": "%d SMs x 128 FP32 FMA lanes x 2 x %.0f MHz" % (nsm, mhz)}}
+    # ---- the full-rank bias proxy: unadjusted iterations on the headline ensemble
+    pr = workloads.banana()
+    tg = laps.Target.from_problem(pr)
+    x0 = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
+    fr = {"workload": "banana_d100_M4096, unadjusted iterations at a fixed step size"}
+    for K in (0, 20, 100):
+        s = laps.Sampler(tg, pr.M, n_total_steps=5000, fixed_eps=0.01, dtilde_K=K)
+        s.init(x0, seed=seed0)
+        s.step(20)
+        fr["us_per_iteration_K%d" % K] = timed_ms(lambda: s.step(500)) / 500 * 1e3
+    out["fullrank"] = fr
     return out
 
 
