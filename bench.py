@@ -312,6 +312,60 @@ def _forms(flush, stream, mhz, seed0):
     return out
 
 
+def ablations():
+    """The paper's ablations on the synthetic stand-ins, one JSON object:
+    - mams_only: the adjusted phase alone (switch forced after the first step,
+      so the diagonal preconditioner comes from the first ensemble and the step
+      size from the bisection) against LAPS (Table "mams");
+    - fixed_step: the unadjusted phase at fixed step sizes, multiples of the
+      adaptive run's final one, against the adaptive schedule (Fig. "stepsize");
+    - chains: LAPS against the number of chains M (Fig. "chains").
+    Reported per run: gradient evaluations per chain until b^2 < 0.01 (None
+    if never), its wall time, and the final b^2."""
+    import torch
+    from paper_2601_16696_gb300 import build, laps, workloads
+    build.build()
+    torch.cuda.set_device(0)
+
+    def go(pr, key, **cfg):
+        tg = laps.Target.from_problem(pr)
+        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, stop_b2=0.01,
+                         stop_b2_max=1 if key == "b2_max" else 0, **cfg)
+        s.set_truth(pr.Ex2, pr.Varx2)
+        s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=11)
+        s.run()
+        st = s.stats()
+        hit = st["b2_first_t"] >= 0
+        return {"grads_to_b2": st["b2_first_grads"] if hit else None,
+                "ms_to_b2": st["b2_first_ns"] / 1e6 if hit else None,
+                "t_switch": st["t_switch"], "final_" + key: st[key], "eps": st["eps"]}
+
+    out = {"b2_threshold": 0.01, "seed": 11}
+    mo = {}
+    for name, pr, key in (("banana_d100_M4096", workloads.banana(), "b2_max"),
+                          ("gauss_d100_M256", workloads.gauss_diag(), "b2_avg"),
+                          ("icg_d100_M4096", workloads.icg(), "b2_max")):
+        mo[name] = {"b2": key, "laps": go(pr, key), "mams_only": go(pr, key, force_switch_at=1)}
+    out["mams_only"] = mo
+    pr = workloads.gauss_diag()
+    base = go(pr, "b2_avg", adjusted=0)
+    ref = laps.Sampler(laps.Target.from_problem(pr), pr.M, n_total_steps=pr.n_steps)
+    ref.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=11)
+    ref.step(400)
+    eps_end = ref.stats()["eps"]
+    fs = {"workload": "gauss_d100_M256, unadjusted only", "b2": "b2_avg", "adaptive": base,
+          "eps_adaptive_at_t400": eps_end}
+    for f in (0.5, 1.0, 2.0, 4.0):
+        fs["fixed_%gx" % f] = go(pr, "b2_avg", fixed_eps=f * eps_end, adjusted=0)
+    out["fixed_step"] = fs
+    ch = {"workload": "gauss_d100, 2000 steps", "b2": "b2_avg"}
+    for M in (32, 64, 128, 256, 512, 1024, 4096):
+        ch["M%d" % M] = go(workloads.gauss_diag(M=M), "b2_avg")
+    out["chains"] = ch
+    print(json.dumps(out))
+    return 0
+
+
 def ncu_case(adjusted: bool = False):
     import torch
     from paper_2601_16696_gb300 import build, laps, workloads
@@ -345,7 +399,12 @@ def main():
                          "iterations after two others (the case profiled under ncu)")
     ap.add_argument("--ncu-case-adjusted", action="store_true",
                     help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
+    ap.add_argument("--ablations", action="store_true",
+                    help="no contract line: the paper's ablations (MAMS only, fixed step, "
+                         "number of chains) as one JSON object")
     args = ap.parse_args()
+    if args.ablations:
+        return ablations()
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case or args.ncu_case_adjusted:
