@@ -54,11 +54,26 @@ typedef enum {
     LAPS_BANANA = 1,      /* pairs (a,b) = (x_2k, x_2k+1): a ~ N(0,1), b|a ~ N(a^2, sb^2); d even */
     LAPS_FUNNEL = 2,      /* v = x_0 ~ N(0, sv^2), x_i|v ~ N(0, e^v), i = 1..d-1 */
     LAPS_LOGREG = 3,      /* sum_n [y_n z_n - softplus(z_n)] - |w|^2/(2 prior_var), z = X w */
-    LAPS_GAUSS_DENSE = 4  /* -1/2 x^T P x with a dense symmetric positive-definite precision P
+    LAPS_GAUSS_DENSE = 4, /* -1/2 x^T P x with a dense symmetric positive-definite precision P
                              (Sec. 6, the randomly oriented ill-conditioned Gaussian); d <= 512;
                              sampled on the streamed path, its gradient -P x as one
                              chains-by-coordinates contraction per step */
+    LAPS_USER = 5         /* the caller's log-density: user_fn (below) evaluates it and its
+                             gradient for the ensemble's points at every gradient evaluation;
+                             d <= 512; sampled on the streamed path */
 } laps_target_kind;
+
+/* Log-density of a LAPS_USER target (Sec. 1: the user supplies log p and its
+ * gradient).  Called on the host thread that enqueues the sampler's work,
+ * once per gradient evaluation of the ensemble (not fused with the chain
+ * updates).  x: device [M][ld] points, row stride ld >= d floats, entries
+ * past d are zero; logp: device [M] output; grad: device [M][ld] output,
+ * entries past d ignored.  The function must enqueue its work on `stream`
+ * (a cudaStream_t), must not synchronise it, and must not keep the pointers
+ * after it returns.  Return 0 on success; any other value makes the calling
+ * laps entry point return LAPS_ERR_CUDA with a message naming the callback. */
+typedef int (*laps_logp_grad_fn)(const float* x, int64_t M, int64_t ld, float* logp, float* grad,
+                                 void* stream, void* user_data);
 
 /* Arithmetic of the logistic-regression contraction in the unadjusted phase. */
 typedef enum {
@@ -78,6 +93,8 @@ typedef struct {
     const float* X;         /* LOGREG: device [n_data][d] design matrix (intercept included) */
     const float* y;         /* LOGREG: device [n_data] labels in {0, 1} */
     double prior_var;       /* LOGREG: prior variance of each weight (1) */
+    laps_logp_grad_fn user_fn; /* USER: the log-density callback */
+    void* user_data;        /* USER: passed to user_fn unchanged */
 } laps_target_desc;
 
 typedef struct laps_target laps_target;

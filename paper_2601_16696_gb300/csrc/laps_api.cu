@@ -321,6 +321,11 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
         if ((d + 63) / 64 * 64 > kLogregMaxKp)
             return fail(LAPS_ERR_UNSUPPORTED, "LOGREG is built for d <= " + std::to_string(kLogregMaxKp));
         break;
+    case LAPS_USER:
+        if (!desc->user_fn) return fail(LAPS_ERR_INVALID_ARG, "USER needs user_fn");
+        if (d > kDenseMaxDim)
+            return fail(LAPS_ERR_UNSUPPORTED, "USER targets are built for d <= " + std::to_string(kDenseMaxDim));
+        break;
     case LAPS_GAUSS_DENSE:
         if (!desc->prec || !aligned(desc->prec, 4))
             return fail(LAPS_ERR_INVALID_ARG, "GAUSS_DENSE needs a device prec[d][d]");

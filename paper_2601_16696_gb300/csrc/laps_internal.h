@@ -52,6 +52,7 @@ struct laps_ctx {
     // streamed path (targets whose gradient is an ensemble contraction)
     bool streamed = false;
     float *yw = nullptr, *uw = nullptr, *W = nullptr, *gpart = nullptr;
+    float* ulp = nullptr;            // USER targets: the callback's FP32 log p [M]
     float2 *dlw = nullptr, *lpw = nullptr, *lpart = nullptr;
     int* go = nullptr;
     int nsplit = 1, seg_cpl = 0, seg_G = 0, fin_G = 0, adj_integ = 0;
@@ -95,7 +96,11 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st);
 constexpr int kDenseMaxDim = 512;
 cudaError_t gauss_dense_grad(const float* P, int d_pad, int d, const float* W, int64_t M, float* G,
                              float2* LP, cudaStream_t st);
-inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_GAUSS_DENSE; }
+inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_GAUSS_DENSE || kind == TGT_USER; }
+// USER targets: calls the callback for W [M][ld] and converts its FP32 log p into
+// the float-float partial the chain updates read (lp32: device [M] scratch)
+laps_status user_grad(const laps_target* tg, const float* W, int64_t M, int ld, float* G, float* lp32,
+                      float2* LP, cudaStream_t st);
 laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
                                  float2* lpart, cudaStream_t st);
 laps_status status_error(int device_status);

@@ -24,7 +24,7 @@ struct Hyper {
     int nonfinite_last, b2_first_t;
 };
 
-enum : int { TGT_GAUSS = 0, TGT_BANANA = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DENSE = 4 };
+enum : int { TGT_GAUSS = 0, TGT_BANANA = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DENSE = 4, TGT_USER = 5 };
 enum : int { INTEG_LF = 0, INTEG_MN2 = 1, INTEG_MN4 = 2 };
 enum : int { TAG_X0 = 0, TAG_O1 = 1, TAG_O2 = 2, TAG_REFRESH = 3, TAG_MH = 4, TAG_Z = 5 };
 

@@ -409,6 +409,7 @@ laps_status launch_grad(laps_ctx* c, bool mma, cudaStream_t st) {
         e = gauss_dense_grad(c->tg->prec_dense, c->d_pad, c->d, c->W, c->M, c->gpart, c->lpart, st);
         return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
     }
+    if (c->tg->kind == TGT_USER) return user_grad(c->tg, c->W, c->M, c->d_pad, c->gpart, c->ulp, c->lpart, st);
     if (mma)
         e = logreg_grad_mma(c->tg->lr, c->tmW, c->W, c->M, c->nsplit_mma, c->rps_mma, c->gpart, c->lpart,
                             c->status, c->cfg.barrier_timeout_ns, st);
@@ -530,7 +531,7 @@ laps_status streamed_setup(laps_ctx* c) {
     // data splits of the gradient: about two blocks of 64 chains per SM
     const int64_t tiles = (c->M + 63) / 64;
     c->nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * nsm + tiles - 1) / tiles));
-    if (c->tg->kind == TGT_GAUSS_DENSE) c->nsplit = 1;  // one block holds every coordinate of its chains
+    if (c->tg->kind != TGT_LOGREG) c->nsplit = 1;  // one evaluation writes every coordinate of its chains
     c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
     coefs_table(c->cf);
     if (c->cfg.precision == LAPS_MIXED) {
@@ -556,6 +557,7 @@ laps_status streamed_alloc(laps_ctx* c) {
               alloc((void**)&c->lpw, c->M * 8) && alloc((void**)&c->gpart, (size_t)S * Md * 4) &&
               alloc((void**)&c->lpart, (size_t)S * c->M * 8) && alloc((void**)&c->go, 4 * sizeof(int));
     if (ok && c->mixed) ok = alloc(&c->Wb, (size_t)c->M_pad * 2 * c->d_pad * 2);
+    if (ok && c->tg->kind == TGT_USER) ok = alloc((void**)&c->ulp, (size_t)c->M * 4);
     if (!ok) return fail(LAPS_ERR_OOM, "device allocation of the streamed working state failed");
     if (cudaMallocHost((void**)&c->h_hyper, sizeof(Hyper)) != cudaSuccess)
         return fail(LAPS_ERR_OOM, "pinned host allocation failed");

@@ -95,6 +95,27 @@ __global__ void logreg_unpack_kernel(const float* __restrict__ G, const float2* 
     }
 }
 
+// USER targets: the callback's FP32 log p as the float-float partial the chain
+// updates read, and the gradient's padding columns cleared (the sampler's norms
+// and dot products run over the padded rows)
+__global__ void user_after_kernel(const float* __restrict__ lp, float2* __restrict__ LP, float* __restrict__ G,
+                                  int64_t M, int d, int ld) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        LP[m] = make_float2(lp[m], 0.0f);
+        for (int i = d; i < ld; ++i) G[m * ld + i] = 0.0f;
+    }
+}
+
+laps_status user_grad(const laps_target* tg, const float* W, int64_t M, int ld, float* G, float* lp32,
+                      float2* LP, cudaStream_t st) {
+    const int r = tg->desc.user_fn(W, M, ld, lp32, G, (void*)st, tg->desc.user_data);
+    if (r != 0) return fail(LAPS_ERR_CUDA, "user_fn returned " + std::to_string(r));
+    const int blocks = (int)std::min<int64_t>((M + 255) / 256, 4096);
+    user_after_kernel<<<blocks, 256, 0, st>>>(lp32, LP, G, M, tg->d, ld);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "user_after_kernel");
+}
+
 // targets evaluated by an ensemble contraction (LOGREG, GAUSS_DENSE): the points
 // packed to the contraction's padded rows, its partials back to [M][d]
 static laps_status streamed_logp_grad(const laps_target* tg, const float* x, int64_t M, float* logp,
@@ -192,6 +213,10 @@ extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float*
                                              float* logp, float* grad, void* stream) {
     if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (M == 0) return LAPS_OK;
+    if (tg->kind == TGT_USER) {
+        const int r = tg->desc.user_fn(x, M, tg->d, logp, grad, stream, tg->desc.user_data);
+        return r == 0 ? LAPS_OK : fail(LAPS_ERR_CUDA, "user_fn returned " + std::to_string(r));
+    }
     if (streamed_kind(tg->kind)) return streamed_logp_grad(tg, x, M, logp, grad, (cudaStream_t)stream);
     const int threads = 256;
     const int64_t blocks = (M * 32 + threads - 1) / threads;

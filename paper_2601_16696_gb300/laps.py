@@ -18,7 +18,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblaps.so")
 
-GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE = 0, 1, 2, 3, 4
+GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE, USER = 0, 1, 2, 3, 4, 5
 FP32, MIXED = 0, 1
 LF, MN2, MN4 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NONFINITE",
@@ -31,10 +31,25 @@ class LapsError(RuntimeError):
         self.status = status
 
 
+# int (*)(const float* x, int64 M, int64 ld, float* logp, float* grad, void* stream, void* user)
+LOGP_GRAD_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p)
+
+
 class TargetDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("d", C.c_int64), ("prec", C.c_void_p),
                 ("banana_sb", C.c_double), ("funnel_sv", C.c_double), ("n_data", C.c_int64),
-                ("X", C.c_void_p), ("y", C.c_void_p), ("prior_var", C.c_double)]
+                ("X", C.c_void_p), ("y", C.c_void_p), ("prior_var", C.c_double),
+                ("user_fn", LOGP_GRAD_FN), ("user_data", C.c_void_p)]
+
+
+class _DeviceView:
+    """A float32 device array given by pointer, shape and byte strides, for
+    torch.as_tensor (zero-copy, through __cuda_array_interface__)."""
+
+    def __init__(self, ptr: int, shape, strides):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": "<f4", "strides": tuple(strides), "version": 3}
 
 
 class Config(C.Structure):
@@ -213,6 +228,38 @@ class Target:
         h = C.c_void_p()
         _check(lib().laps_target_create(C.byref(desc), C.byref(h)))
         self._h = h
+
+    @classmethod
+    def from_callable(cls, d: int, fn):
+        """A LAPS_USER target: fn(x, logp, grad) receives torch views of the
+        ensemble's points x [M, d] and fills logp [M] and grad [M, d] (grad log p)
+        with torch operations.  It runs on the sampler's stream, once per
+        gradient evaluation; an exception in fn makes the sampler call raise."""
+        self = cls.__new__(cls)
+        self.kind, self.d, self._keep, self._errors = USER, d, [], []
+
+        def cb(x, M, ld, lp, g, stream, user):
+            try:
+                if M == 0:
+                    return 0
+                xv = torch.as_tensor(_DeviceView(x, (M, ld), (4 * ld, 4)), device="cuda")[:, :d]
+                gv = torch.as_tensor(_DeviceView(g, (M, ld), (4 * ld, 4)), device="cuda")[:, :d]
+                lv = torch.as_tensor(_DeviceView(lp, (M,), (4,)), device="cuda")
+                st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(st):
+                    fn(xv, lv, gv)
+                return 0
+            except Exception as e:  # reported by the laps call that made this one
+                self._errors.append(e)
+                return 1
+
+        cfn = LOGP_GRAD_FN(cb)
+        self._keep.append(cfn)
+        desc = TargetDesc(USER, d, None, 0.1, 3.0, 0, None, None, 1.0, cfn, None)
+        h = C.c_void_p()
+        _check(lib().laps_target_create(C.byref(desc), C.byref(h)))
+        self._h = h
+        return self
 
     @classmethod
     def from_problem(cls, pr, device="cuda"):
