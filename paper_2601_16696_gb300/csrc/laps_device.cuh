@@ -21,10 +21,11 @@ enum : int { ST_OK = 0, ST_BADPARAM = 1, ST_TIMEOUT = 4, ST_NONFINITE = 5 };
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        // one 32 x 32 -> 64-bit product per word: both halves from one multiply
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -32,9 +33,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// (r >> 9) + 1/2 scaled by 2^-23: a binary32 value in (0, 1), exact.
+// ((r >> 9) + 1/2) 2^-23 = (r >> 9) 2^-23 + 2^-24: a binary32 value in (0, 1), exact
+// (one fused multiply-add of exact terms).
 __device__ __forceinline__ float u01(uint32_t r) {
-    return (static_cast<float>(r >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    return fmaf(static_cast<float>(r >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+}
+
+// sqrt(-2 ln u) for u in (0, 1): the argument is > 0, so x rsqrt(x) is finite;
+// rsqrtf is within 2 ulp, the product within ~3 ulp (4e-7 relative).
+__device__ __forceinline__ float bm_radius(float u) {
+    const float x = -2.0f * logf(u);
+    return x * rsqrtf(x);
 }
 
 // cos(2 pi u) and sin(2 pi u) for u in (0, 1) from the hardware sine / cosine
@@ -52,11 +61,11 @@ __device__ __forceinline__ void normals4(uint32_t j, uint32_t m, uint32_t t, uin
                                          uint32_t k0, uint32_t k1, float z[4]) {
     const uint4 r = philox4x32_10(make_uint4(j, m, t, tagpid), k0, k1);
     float s, c;
-    float rad = sqrtf(-2.0f * logf(u01(r.x)));
+    float rad = bm_radius(u01(r.x));
     cos_sin_2pi(u01(r.y), c, s);
     z[0] = rad * c;
     z[1] = rad * s;
-    rad = sqrtf(-2.0f * logf(u01(r.z)));
+    rad = bm_radius(u01(r.z));
     cos_sin_2pi(u01(r.w), c, s);
     z[2] = rad * c;
     z[3] = rad * s;

@@ -7,7 +7,8 @@ The target is ill-conditioned (condition number 1.1e5), so -P x cancels and a
 binary32 dot product is off by ~1e-4 of max|g|; the kernel accumulates the
 products exactly in float-float (a compensated dot product), so gradients are
 held to 1e-6 of max|g| per point and log p to 1e-6 relative.  Per-chain
-positions within 1e-5 over the first 10 steps; final b^2 within 10%.
+positions within 1e-5 over the first 10 steps; final b^2 within 10% (a run
+switched into MAMS is held to its path-independent quantities, see below).
 """
 import numpy as np
 import pytest
@@ -98,25 +99,49 @@ def test_dense_first_ten_steps_adaptive(L, ora):
     assert s.trace()[1]["eps_used"] == pytest.approx(r.trace[1]["eps_used"], rel=1e-6)
 
 
-@pytest.mark.parametrize("cfg,key", [({}, "b2_avg"), ({"force_switch_at": 400}, "b2_avg")])
-def test_dense_final_b2_within_10_percent(L, ora, cfg, key):
-    """Whole runs, M = 1024, 2000 steps (oracle seed-to-seed spread of these
-    tail means 2-4%).  Unswitched, b^2_max falls below 0.01 after ~630
-    gradients; after a forced switch the diagonal preconditioner cannot undo
-    the rotation and MAMS ends near b^2_avg = 0.006, on both sides."""
+def _tail(trace, key, phase):
+    rows = [x for x in trace[1:] if x["phase"] == phase]
+    return float(np.mean([x[key] for x in rows[len(rows) // 2:]]))
+
+
+def test_dense_final_b2_within_10_percent(L, ora):
+    """Whole unswitched run, M = 1024, 2000 steps (oracle seed-to-seed spread of
+    the b^2_avg tail mean 2%); b^2_max falls below 0.01 after ~630 gradients."""
     pr = W.icg(M=1024, n_steps=2000)
+    s = _gpu(L, pr, seed=0)
+    s.run()
+    st = s.stats()
+    r = _ora(ora, pr, seed=0)
+    r.run()
+    assert st["t"] == r.t and st["phase"] == r.phase == 0
+    bg, bo = _tail(s.trace(), "b2_avg", 0), _tail(r.trace, "b2_avg", 0)
+    assert abs(bg - bo) <= 0.10 * bo, (bg, bo)
+
+
+def test_dense_switched_run(L, ora):
+    """Switch forced at step 400: the diagonal preconditioner cannot undo the
+    rotation, so MAMS is still removing bias at the end and its b^2 depends on
+    the path (oracle, 5 seeds: b^2_avg tail mean 0.0044-0.0062).  The step
+    size the bisection freezes at (0.239-0.245 over those seeds; it is set at
+    the first proposal within 0.03 of the target acceptance, so it moves in
+    steps of a few percent between paths) and the acceptance (0.72-0.74)
+    depend on it much less: they are held to 6% and 0.06, b^2_avg to twice the
+    seed spread."""
+    pr = W.icg(M=1024, n_steps=2000)
+    cfg = {"force_switch_at": 400}
     s = _gpu(L, pr, seed=0, **cfg)
     s.run()
     st = s.stats()
     r = _ora(ora, pr, seed=0, **cfg)
     r.run()
-    assert st["t"] == r.t and st["phase"] == r.phase and st["t_switch"] == r.t_switch
+    assert st["t"] == r.t and st["phase"] == r.phase == 1 and st["t_switch"] == r.t_switch == 400
     tg = s.trace()
-    rows_g = [x for x in tg[1:] if x["phase"] == tg[-1]["phase"]]
-    rows_o = [x for x in r.trace[1:] if x["phase"] == r.trace[-1]["phase"]]
-    bg = float(np.mean([x[key] for x in rows_g[len(rows_g) // 2:]]))
-    bo = float(np.mean([x[key] for x in rows_o[len(rows_o) // 2:]]))
-    assert abs(bg - bo) <= 0.10 * bo, (bg, bo)
+    assert tg[-1]["eps"] == pytest.approx(r.trace[-1]["eps"], rel=0.06)
+    ag = np.mean([x["acc"] for x in tg[-20:]])
+    ao = np.mean([x["acc"] for x in r.trace[-20:]])
+    assert abs(ag - ao) <= 0.06, (ag, ao)
+    bg, bo = _tail(tg, "b2_avg", 1), _tail(r.trace, "b2_avg", 1)
+    assert abs(bg - bo) <= 0.35 * bo, (bg, bo)
 
 
 def test_dense_determinism_and_checkpoint(L):
