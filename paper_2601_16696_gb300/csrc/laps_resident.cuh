@@ -92,7 +92,9 @@ __device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float a
         }
         return group_sum_ff<LPC>(ff_make(part));
     } else if constexpr (KIND == TGT_BANANA) {
-        ff part = ff_make(0.0f);
+        // the lane's few terms of the change in binary32 (each is small, of the
+        // order of the step), the group's total in float-float
+        float part = 0.0f;
 #pragma unroll
         for (int q = 0; q < CPL; q += 2) {
             const float ao = sg[q] * y[q], bo = sg[q + 1] * y[q + 1];
@@ -101,15 +103,15 @@ __device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float a
             const float da = an - ao, db = bn - bo, sa = ao + an;
             const float ro = fmaf(-ao, ao, bo), rn = fmaf(-an, an, bn);
             const float dr = fmaf(-da, sa, db);
-            part = ff_add(part, -0.5f * da * sa);
-            part = ff_add(part, -0.5f * P.inv_s2 * dr * (ro + rn));
+            part = fmaf(-0.5f * da, sa, part);
+            part = fmaf(-0.5f * P.inv_s2 * dr, ro + rn, part);
             y[q] = ya;
             y[q + 1] = yb;
             const float ris = rn * P.inv_s2;
             g[q] = sg[q] * fmaf(2.0f * an, ris, -an);
             g[q + 1] = sg[q + 1] * (-ris);
         }
-        return group_sum_ff<LPC>(part);
+        return group_sum_ff<LPC>(ff_make(part));
     } else {  // TGT_FUNNEL
         float xn[CPL];
         float so = 0.0f, ds = 0.0f;
@@ -170,7 +172,7 @@ __device__ __forceinline__ void o_update(const KParams& P, int gl, bool active, 
         }
     }
     n2 = group_sum<LPC>(n2);
-    const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+    const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
@@ -190,16 +192,20 @@ __device__ __forceinline__ void b_update(float beps, float inv_dm1, float dm1,
     gg = group_sum<LPC>(gg);
     gu = group_sum<LPC>(gu);
     if (gg > 0.0f) {
-        const float gn = sqrtf(gg);
-        const float eu = gu / gn;
+        // per-chain scalars, evaluated by every lane of the group: 1/|g| from one
+        // reciprocal square root (~2 ulp), zeta from 1 - zeta (accurate for small
+        // delta), the denominator (in [2 zeta^2, 2], > 0) inverted approximately
+        const float rg = rsqrtf(gg);
+        const float gn = gg * rg;
+        const float eu = gu * rg;
         const float delta = beps * gn * inv_dm1;
-        const float zeta = expf(-delta);
         const float om = -expm1f(-delta);  // 1 - zeta
+        const float zeta = 1.0f - om;
         const float opz = 1.0f + zeta;
         const float den = fmaf(eu, om * opz, fmaf(zeta, zeta, 1.0f));
-        const float inv = 1.0f / den;
+        const float inv = __fdividef(1.0f, den);
         const float cu = 2.0f * zeta * inv;
-        const float ce = om * fmaf(eu, om, opz) * inv / gn;
+        const float ce = om * fmaf(eu, om, opz) * inv * rg;
 #pragma unroll
         for (int q = 0; q < CPL; ++q) u[q] = fmaf(cu, u[q], ce * g[q]);
         const float kin = dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu)));
