@@ -131,7 +131,7 @@ __device__ __forceinline__ void g_o(const KParams& P, Grp& G, uint32_t m, uint32
         }
     }
     n2 = gsum1(G, n2);
-    const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+    const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
@@ -225,16 +225,19 @@ __device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float 
                                           float gg, float gu, const float (&y)[CPL], float (&u)[CPL], ff& dl,
                                           const float4* s_pr4, const float4* s_sg4) {
     if (!(gg > 0.0f)) return;
-    const float gn = sqrtf(gg);
-    const float eu = gu / gn;
+    // per-chain scalars as in the resident kernel's B: 1/|g| from one reciprocal
+    // square root, zeta from 1 - zeta, the positive denominator inverted approximately
+    const float rg = rsqrtf(gg);
+    const float gn = gg * rg;
+    const float eu = gu * rg;
     const float delta = beps * gn * inv_dm1;
-    const float zeta = expf(-delta);
     const float om = -expm1f(-delta);
+    const float zeta = 1.0f - om;
     const float opz = 1.0f + zeta;
     const float den = fmaf(eu, om * opz, fmaf(zeta, zeta, 1.0f));
-    const float inv = 1.0f / den;
+    const float inv = __fdividef(1.0f, den);
     const float cu = 2.0f * zeta * inv;
-    const float ce = om * fmaf(eu, om, opz) * inv / gn;
+    const float ce = om * fmaf(eu, om, opz) * inv * rg;
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         float g[4];
@@ -254,7 +257,7 @@ __device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF
     float s[3] = {0.0f, 0.0f, 0.0f};
     g_o_mix<CPL, true>(P, G, m, t, TAG_O1, c1, c2s, u, y, s_pr4, s_sg4, s);
     gsum<3>(G, s);
-    float inv = s[0] > 0.0f ? 1.0f / sqrtf(s[0]) : 0.0f;
+    float inv = s[0] > 0.0f ? rsqrtf(s[0]) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
     float gg = s[2], gu = s[1] * inv;
@@ -304,7 +307,7 @@ __device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF
     } else {
         s2[0] = gsum1(G, s2[0]);
     }
-    inv = s2[0] > 0.0f ? 1.0f / sqrtf(s2[0]) : 0.0f;
+    inv = s2[0] > 0.0f ? rsqrtf(s2[0]) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                             }
                         }
                         n2 = gsum1(Gc, n2);
-                        const float inv = n2 > 0.0f ? 1.0f / sqrtf(n2) : 0.0f;
+                        const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) u[q] *= inv;
                         const uint32_t t0 = (uint32_t)sH.t;
