@@ -4,7 +4,7 @@
 // points as one chains-by-coordinates contraction G = -W P.
 //
 // A block owns 8 CW chains: their points stay in shared memory, P streams
-// through shared memory 32 rows at a time, warp w accumulates chains
+// through shared memory 32 rows at a time (rows up to d only), warp w accumulates chains
 // CW w .. CW w + CW - 1 and lane l the columns l, l + 32, ... (conflict-free row
 // reads of P, broadcast reads of the points).
 //
@@ -49,13 +49,15 @@ __global__ void __launch_bounds__(kThreads) gauss_dense_grad_kernel(const float*
     for (int c = 0; c < CW; ++c)
 #pragma unroll
         for (int q = 0; q < Q; ++q) hi[c][q] = lo[c][q] = 0.0f;
-    for (int k0 = 0; k0 < dp; k0 += kRows) {
+    for (int k0 = 0; k0 < d; k0 += kRows) {
         __syncthreads();  // the points are staged; the previous rows are consumed
         for (int o = tid; o < kRows * dp / 4; o += kThreads)
             reinterpret_cast<float4*>(Ps)[o] = reinterpret_cast<const float4*>(P + (size_t)k0 * dp)[o];
         __syncthreads();
+        // rows past d of P are zero: they would add exact zeros, so stop at d
+        const int kn = d - k0 < kRows ? d - k0 : kRows;
 #pragma unroll 2
-        for (int kk = 0; kk < kRows; ++kk) {
+        for (int kk = 0; kk < kn; ++kk) {
             float p[Q], x[CW];
 #pragma unroll
             for (int q = 0; q < Q; ++q) p[q] = Ps[kk * dp + lane + 32 * q];
@@ -97,7 +99,9 @@ __global__ void __launch_bounds__(kThreads) gauss_dense_grad_kernel(const float*
 
 template <int Q>
 cudaError_t launch_q(const float* P, int d, const float* W, int64_t M, float* G, float2* LP, cudaStream_t st) {
-    constexpr int CW = Q <= 4 ? 4 : Q <= 8 ? 2 : 1;  // accumulators: 2 CW Q registers
+    // accumulators: 2 CW Q registers; 8 CW chains per block, so that the ensembles
+    // of a few thousand chains give every SM a block or more
+    constexpr int CW = Q <= 8 ? 2 : 1;
     const size_t smem = (size_t)(8 * CW + kRows) * 32 * Q * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(gauss_dense_grad_kernel<Q, CW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
