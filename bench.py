@@ -312,6 +312,39 @@ def _forms(flush, stream, mhz, seed0):
     return out
 
 
+def ncu_case_form(which: str):
+    """No timing: small cases of the other kernels, for ncu captures (a few hundred
+    MB on the device at most).  logreg: the mixed-precision run of the logistic
+    regression, tcgen05 gradient launches 1 (init) to 4; batch: 32 problems of the
+    batch (d < 10^4, 33 M coordinates), batch_kernel launch 1 (init), 2 and 3 (5
+    unadjusted iterations each); dense: the ill-conditioned Gaussian, gradient
+    launches 1 (init) to 4."""
+    import torch
+    from paper_2601_16696_gb300 import build, laps, workloads
+    build.build()
+    info = {"ncu_case": which}
+    if which == "logreg":
+        pr = workloads.logreg()
+        s = laps.Sampler(laps.Target.from_problem(pr), pr.M, n_total_steps=pr.n_steps, precision=1)
+        s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)
+        s.step(3)
+    elif which == "batch":
+        probs = [p for p in workloads.batch64() if p.d < 10000][:32]
+        b = laps.Batch(probs, use_x0=False, n_total_steps=2000)
+        b.init(seed=0)
+        b.step(5)
+        b.step(5)
+        info.update(coordinates=sum(p.d * p.M for p in probs), shape=b.shape())
+    else:
+        pr = workloads.icg()
+        s = laps.Sampler(laps.Target.from_problem(pr), pr.M, n_total_steps=pr.n_steps)
+        s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)
+        s.step(3)
+    torch.cuda.synchronize()
+    print(json.dumps(info))
+    return 0
+
+
 def ablations():
     """The paper's ablations on the synthetic stand-ins, one JSON object:
     - mams_only: the adjusted phase alone (switch forced after the first step,
@@ -399,12 +432,16 @@ def main():
                          "iterations after two others (the case profiled under ncu)")
     ap.add_argument("--ncu-case-adjusted", action="store_true",
                     help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
+    ap.add_argument("--ncu-case-form", choices=["logreg", "batch", "dense"],
+                    help="no timing: a small case of another kernel (for ncu)")
     ap.add_argument("--ablations", action="store_true",
                     help="no contract line: the paper's ablations (MAMS only, fixed step, "
                          "number of chains) as one JSON object")
     args = ap.parse_args()
     if args.ablations:
         return ablations()
+    if args.ncu_case_form:
+        return ncu_case_form(args.ncu_case_form)
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case or args.ncu_case_adjusted:
