@@ -52,6 +52,19 @@ def _rank_env():
     return r, w, lr
 
 
+def _max_over_ranks(x: float) -> float:
+    """The largest value over the ranks of the process group (a job's time is
+    its slowest rank's); x itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -509,12 +522,7 @@ def main():
     barrier()
     st = sampler.stats()
     assert st["done"] and st["grads"] == grads, st
-    ms = statistics.mean(ts)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(statistics.mean(ts))
     value = world * pr.M * grads / (ms * 1e-3)
 
     # ---- the kernel's own duration and its ALU roofline
@@ -566,7 +574,7 @@ def main():
         out_host.copy_(x0_e2e, non_blocking=True)
 
     te = timed(e2e_run, args.steps, seed_base + 400)
-    e2e_ms = statistics.mean(te)
+    e2e_ms = _max_over_ranks(statistics.mean(te))
     e2e = {"value": world * pr.M * grads / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4,
            "ms_per_step": e2e_ms}
