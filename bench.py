@@ -14,7 +14,9 @@ e2e        the same metric through the public API with host buffers: x0 copied
            from pinned host memory and the samples copied back in the timed
            region.
 time_to_b2 wall time (CUDA events) of runs that stop at b^2_max < 0.01.
-roofline   the persistent kernel against the FP32 ALU issue rate.
+roofline   the persistent kernel against the FP32 ALU issue rate: algorithmic
+           operations of the run (the per-coordinate counts below) over the
+           kernel's own duration, against SMs x 128 lanes x the measured clock.
 cpu_baseline  the FP64 oracle on the host cores on a bounded sample.
 
 --impl reference runs the oracle (the only reference this path has) instead.
@@ -39,8 +41,10 @@ sys.path.insert(0, ROOT)
 METRIC = "chain-gradient-evals/sec and wall time to second-moment bias^2<0.01, 1 GB300"
 UNIT = "chain-grad-evals/s"
 WORKLOAD = dict(name="banana_d100", d=100, M=4096, n_steps=5000, switch_at=1000)
-# algorithmic ALU operations per coordinate and gradient evaluation (the design doc
-# "Roofline of the resident kernel"): LF unadjusted step and MN2 adjusted step
+# algorithmic ALU operations per coordinate and gradient evaluation: an LF
+# unadjusted step (two O maps: a quarter Philox4x32-10 call, half a Box-Muller
+# pair, uniforms and the O arithmetic, 48 each; two B maps, the A map with the
+# target and the ensemble sums, 21) and an MN2 adjusted step per gradient
 ALU_OPS_LF = 117.0
 ALU_OPS_MN2_PER_GRAD = 61.0
 
