@@ -133,6 +133,9 @@ typedef struct {
                                 K > 0: the full-rank D~ by Hutchinson's estimator over K
                                 Rademacher vectors per step (App. B "Full rank"; the paper
                                 uses 100); register-resident targets only */
+    int dense_streamed;      /* GAUSS_DENSE: 0 runs the register-resident kernel (P in shared
+                                memory) when d <= 128 and the streamed path beyond; 1 always
+                                the streamed path */
 } laps_config;
 
 /* Snapshot of the sampler (laps_get_stats). */

@@ -14,6 +14,7 @@ namespace laps {
 const void* resident_kernel_0(int lpc, int cpl, bool fr);
 const void* resident_kernel_1(int lpc, int cpl, bool fr);
 const void* resident_kernel_2(int lpc, int cpl, bool fr);
+const void* resident_kernel_4(int lpc, int cpl, bool fr);
 
 static thread_local std::string g_err;
 
@@ -37,6 +38,7 @@ static const void* resident_fn(int kind, int lpc, int cpl, bool fr) {
     case TGT_GAUSS: return resident_kernel_0(lpc, cpl, fr);
     case TGT_BANANA: return resident_kernel_1(lpc, cpl, fr);
     case TGT_FUNNEL: return resident_kernel_2(lpc, cpl, fr);
+    case TGT_GAUSS_DENSE: return resident_kernel_4(lpc, cpl, fr);
     }
     return nullptr;
 }
@@ -108,11 +110,12 @@ static int resident_qpp(int d_pad, int threads) {
 }
 // largest slice of coordinates a block owns in the reduction
 static int resident_smax(int d, int G) { return (d + G - 1) / G; }
-static size_t resident_smem(int d_pad, int threads, int lpc, int smax, int K) {
+static size_t resident_smem(int d_pad, int threads, int lpc, int smax, int K, int kind) {
     const int nwarps = threads / 32, slots = threads / lpc;
     const int qpp = resident_qpp(d_pad, threads);
     size_t b = (size_t)qpp * nwarps * d_pad * sizeof(float) + (size_t)slots * NCSF * sizeof(float) +
                (size_t)d_pad * sizeof(float) + ((size_t)NQ * smax + NCS) * sizeof(float2);
+    if (kind == TGT_GAUSS_DENSE) b += dense_smem(d_pad, slots);
     return b + fullrank_smem(d_pad, slots, smax, K, threads);
 }
 
@@ -141,7 +144,8 @@ laps_status choose_shape(laps_ctx* c) {
             if (c->cfg.dtilde_K > 0 && threads < c->d_pad) continue;
             const int cpb = threads / lpc;
             const int G = (int)((c->M + cpb - 1) / cpb);
-            const size_t smem = resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G), c->cfg.dtilde_K);
+            const size_t smem =
+                resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G), c->cfg.dtilde_K, kind);
             if (smem > 200 * 1024) continue;
             CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int bps = 0;
@@ -181,7 +185,7 @@ void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, K
     P.kind = c->tg->kind;
     P.inv_s2 = (float)(1.0 / (c->tg->desc.banana_sb * c->tg->desc.banana_sb));
     P.inv_sv2 = (float)(1.0 / (c->tg->desc.funnel_sv * c->tg->desc.funnel_sv));
-    P.prec = c->tg->prec_pad;
+    P.prec = c->tg->kind == TGT_GAUSS_DENSE ? c->tg->prec_dense : c->tg->prec_pad;
     P.y = c->y;
     P.u = c->u;
     P.g = c->g;
@@ -420,8 +424,13 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
         !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0 || cfg->dtilde_K < 0 ||
         cfg->dtilde_K > 1024)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
-    if (cfg->dtilde_K > 0 && streamed_kind(tg->kind))
-        return fail(LAPS_ERR_UNSUPPORTED, "the full-rank bias proxy is built for the register-resident targets");
+    // GAUSS_DENSE runs in the register-resident kernel while P fits its shared memory
+    const bool streamed = streamed_kind(tg->kind) &&
+                          !(tg->kind == TGT_GAUSS_DENSE && tg->d_pad <= kDenseResidentMax && !cfg->dense_streamed);
+    if (cfg->dtilde_K > 0 && (streamed || tg->kind == TGT_GAUSS_DENSE))
+        return fail(LAPS_ERR_UNSUPPORTED, "the full-rank bias proxy is built for the diagonal, banana and funnel targets");
+    if (cfg->precision != LAPS_FP32 && tg->kind != TGT_LOGREG)
+        return fail(LAPS_ERR_UNSUPPORTED, "mixed precision applies to LOGREG targets only");
     laps_ctx* c = new laps_ctx();
     c->tg = tg;
     c->M = M;
@@ -430,7 +439,7 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     c->d_pad = tg->d_pad;
     c->T = std::max(2, (int)std::ceil(cfg->window_frac * (double)cfg->n_total_steps));
     c->trace_cap = cfg->n_total_steps + 2;
-    laps_status st = streamed_kind(tg->kind) ? streamed_setup(c) : choose_shape(c);
+    laps_status st = streamed ? streamed_setup(c) : choose_shape(c);
     if (st != LAPS_OK) { delete c; return st; }
     const size_t Md = (size_t)M * c->d_pad;
     auto alloc = [&](void** p, size_t bytes) -> bool {

@@ -125,6 +125,15 @@ __host__ __device__ inline int fr_jsplit(int d_pad, int slots, int K, int thread
     js = js < d_pad / 4 ? js : d_pad / 4;
     return js > 1 ? js : 1;
 }
+// shared memory of the dense-precision Gaussian on the resident kernel (bytes,
+// after the reduction's slice rows): 16 bytes of alignment, P [d_pad][d_pad] and
+// one [d_pad] row of x per chain slot
+__host__ __device__ inline size_t dense_smem(int d_pad, int slots) {
+    return 16 + 4 * ((size_t)d_pad * d_pad + (size_t)slots * d_pad);
+}
+// the largest padded dimension the resident kernel serves it for (P in shared memory)
+constexpr int kDenseResidentMax = 128;
+
 // shared memory of the full-rank proxy (bytes, after the reduction's slice rows):
 // [smax K + 3 threads] float-float for the slice owners, 16 bytes of alignment,
 // y and g [slots][d_pad], s [slots][K4], the shifts ybar' and gbar' [d_pad] each,

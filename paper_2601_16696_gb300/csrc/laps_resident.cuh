@@ -21,10 +21,59 @@ struct Coefs {  // integrator tables (Table "integrators"), copied to shared mem
 };
 
 // ---------------------------------------------------------------- target
+// Dense-precision Gaussian (Sec. 6, the rotated ill-conditioned Gaussian): r = P x
+// for the group's chain.  dsm holds P [d_pad][d_pad] then one [d_pad] row per chain
+// slot of the block.  The lanes stage their coordinates of x in the slot's row;
+// each lane then forms its coordinates of P x over the d columns, reading row j of
+// the symmetric P for column j (float4 reads, consecutive across the group's
+// lanes), every product entering a float-float accumulator exactly (the
+// compensated dot product of Ogita, Rump and Oishi, 2005): at condition numbers
+// near 1e5 a binary32 sum loses ~1e-4 of the gradient to cancellation.
+template <int LPC, int CPL>
+__device__ __forceinline__ void dense_px(const KParams& P, int gl, float* dsm, const float (&x)[CPL],
+                                         float (&r)[CPL]) {
+    const int dp = P.d_pad;
+    const float* sP = dsm;
+    float* sx = dsm + (size_t)dp * dp + (size_t)(threadIdx.x / LPC) * dp;
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = gl + LPC * k;
+        if (j < P.nblk)
+            *reinterpret_cast<float4*>(sx + 4 * j) = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+    }
+    __syncwarp();
+    float hi[CPL], lo[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) hi[q] = lo[q] = 0.0f;
+    for (int jj = 0; jj < P.d; ++jj) {
+        const float xj = sx[jj];
+#pragma unroll
+        for (int k = 0; k < CPL / 4; ++k) {
+            const int j = gl + LPC * k;
+            if (j >= P.nblk) continue;
+            const float4 p4 = *reinterpret_cast<const float4*>(sP + (size_t)jj * dp + 4 * j);
+            const float pc[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int q = 4 * k + c;
+                const float pv = xj * pc[c];
+                const float er = fmaf(xj, pc[c], -pv);  // exact: x_j P_ji = pv + er
+                float sh, sl;
+                two_sum(hi[q], pv, sh, sl);
+                hi[q] = sh;
+                lo[q] += sl + er;
+            }
+        }
+    }
+    __syncwarp();  // the slot's row is rewritten by the next evaluation
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) r[q] = hi[q] + lo[q];
+}
+
 // log p at x = sigma o y and the gradient in y (sigma o grad_x).  Returns the
-// group-wide log p as a compensated float-float.
+// group-wide log p as a compensated float-float.  dsm: GAUSS_DENSE only.
 template <int KIND, int LPC, int CPL>
-__device__ __forceinline__ ff eval_target(const KParams& P, int gl, int lane,
+__device__ __forceinline__ ff eval_target(const KParams& P, int gl, int lane, float* dsm,
                                           const float (&y)[CPL], float (&g)[CPL],
                                           const float (&pr)[CPL], const float (&sg)[CPL]) {
     if constexpr (KIND == TGT_GAUSS) {
@@ -35,6 +84,18 @@ __device__ __forceinline__ ff eval_target(const KParams& P, int gl, int lane,
             const float gx = -pr[q] * xt;
             g[q] = sg[q] * gx;
             part = fmaf(0.5f * gx, xt, part);  // -1/2 prec x^2
+        }
+        return group_sum_ff<LPC>(ff_make(part));
+    } else if constexpr (KIND == TGT_GAUSS_DENSE) {
+        float xt[CPL], r[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) xt[q] = sg[q] * y[q];
+        dense_px<LPC, CPL>(P, gl, dsm, xt, r);
+        float part = 0.0f;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            g[q] = sg[q] * (-r[q]);
+            part = fmaf(-0.5f * xt[q], r[q], part);  // -1/2 x (P x)
         }
         return group_sum_ff<LPC>(ff_make(part));
     } else if constexpr (KIND == TGT_BANANA) {
@@ -76,7 +137,7 @@ __device__ __forceinline__ ff eval_target(const KParams& P, int gl, int lane,
 // difference form (products of x' - x and x' + x), so that the energy error
 // keeps its accuracy when |log p| is large and the change is small.
 template <int KIND, int LPC, int CPL>
-__device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float ae,
+__device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float* dsm, float ae,
                                      float (&y)[CPL], const float (&u)[CPL], float (&g)[CPL],
                                      const float (&pr)[CPL], const float (&sg)[CPL]) {
     if constexpr (KIND == TGT_GAUSS) {
@@ -89,6 +150,26 @@ __device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float a
             part = fmaf(-0.5f * pr[q] * (xn - xo), xo + xn, part);
             y[q] = yn;
             g[q] = sg[q] * (-pr[q] * xn);
+        }
+        return group_sum_ff<LPC>(ff_make(part));
+    } else if constexpr (KIND == TGT_GAUSS_DENSE) {
+        // log p(x') - log p(x) = -1/2 (x' - x)^T P (x' + x) = 1/2 (x' - x).(g_x' + g_x)
+        //                      = 1/2 sum_i (y'_i - y_i)(g_y'_i + g_y_i)
+        float xn[CPL], r[CPL], dy[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const float yn = fmaf(ae, u[q], y[q]);
+            dy[q] = yn - y[q];
+            y[q] = yn;
+            xn[q] = sg[q] * yn;
+        }
+        dense_px<LPC, CPL>(P, gl, dsm, xn, r);
+        float part = 0.0f;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const float gn = sg[q] * (-r[q]);
+            part = fmaf(0.5f * dy[q], gn + g[q], part);
+            g[q] = gn;
         }
         return group_sum_ff<LPC>(ff_make(part));
     } else if constexpr (KIND == TGT_BANANA) {
@@ -218,7 +299,7 @@ __device__ __forceinline__ void b_update(float beps, float inv_dm1, float dm1,
 // with y on exit (first-same-as-last gradient reuse).
 template <int KIND, int LPC, int CPL>
 __device__ __forceinline__ void phi_step(const KParams& P, const Coefs& cf, int integ, float eps,
-                                         int gl, int lane, float (&y)[CPL], float (&u)[CPL],
+                                         int gl, int lane, float* dsm, float (&y)[CPL], float (&u)[CPL],
                                          float (&g)[CPL], ff& lp, ff& dl, const float (&pr)[CPL],
                                          const float (&sg)[CPL]) {
     const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
@@ -227,7 +308,7 @@ __device__ __forceinline__ void phi_step(const KParams& P, const Coefs& cf, int 
         b_update<LPC, CPL>(cf.b[integ][k] * eps, inv_dm1, dm1, g, u, dl);
         if (k < K - 1) {
             const float ae = cf.a[integ][k] * eps;
-            const ff dlp = a_step<KIND, LPC, CPL>(P, gl, lane, ae, y, u, g, pr, sg);
+            const ff dlp = a_step<KIND, LPC, CPL>(P, gl, lane, dsm, ae, y, u, g, pr, sg);
             dl = ff_add(dl, ff_neg(dlp));  // -log p(x') + log p(x)
             lp = ff_add(lp, dlp);
         }

@@ -26,10 +26,14 @@ namespace laps {
 template <int KIND>
 struct ResidentDispatch {
     static const void* fn(int lpc, int cpl, bool fr) {
-#define LAPS_FN(L, C)                                                                         \
-    if (lpc == L && cpl == C)                                                                 \
-        return fr ? reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, true>)    \
-                  : reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, false>);
+#define LAPS_FN(L, C)                                                                            \
+    if (lpc == L && cpl == C) {                                                                  \
+        if constexpr (KIND == TGT_GAUSS_DENSE) /* no full-rank form */                           \
+            return fr ? nullptr : reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, false>); \
+        else                                                                                     \
+            return fr ? reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, true>)   \
+                      : reinterpret_cast<const void*>(&laps_resident_kernel<KIND, L, C, false>); \
+    }
         LAPS_SHAPES(LAPS_FN)
 #undef LAPS_FN
         return nullptr;

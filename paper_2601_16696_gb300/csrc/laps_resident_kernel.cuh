@@ -260,6 +260,15 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     float* f_my = f_s + (size_t)slots * K4;                  // [dp] shift ybar'
     float* f_mg = f_my + dp;                                 // [dp] shift gbar'
     uint32_t* f_z = reinterpret_cast<uint32_t*>(f_mg + dp);  // [nzw][K4] Rademacher words
+    // dense-precision Gaussian only: P [dp][dp], then one row of x per chain slot,
+    // after the reduction's rows (dense_smem() sizes it)
+    float* dsm = nullptr;
+    if constexpr (KIND == TGT_GAUSS_DENSE) {
+        dsm = reinterpret_cast<float*>(
+            (reinterpret_cast<uintptr_t>(s_q + (size_t)NQ * P.smax + NCS) + 15) & ~(uintptr_t)15);
+        for (int o = tid; o < dp * dp / 4; o += blockDim.x)
+            reinterpret_cast<float4*>(dsm)[o] = reinterpret_cast<const float4*>(P.prec)[o];
+    }
 
     if (tid == 0) {
         H = *P.hyper;
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 }
             }
         }
-        lp = eval_target<KIND, LPC, CPL>(P, gl, lane, y, g, pr, sg);
+        lp = eval_target<KIND, LPC, CPL>(P, gl, lane, dsm, y, g, pr, sg);
         float n2 = 0.0f;
 #pragma unroll
         for (int q = 0; q < CPL; ++q) n2 = fmaf(g[q], g[q], n2);
@@ -364,7 +373,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             if (H.phase == 0) {
                 const uint32_t t = (uint32_t)H.t;
                 o_update<LPC, CPL>(P, gl, active, m, t, TAG_O1, c1, c2s, u);
-                phi_step<KIND, LPC, CPL>(P, CF, INTEG_LF, eps, gl, lane, y, u, g, lp, dl, pr, sg);
+                phi_step<KIND, LPC, CPL>(P, CF, INTEG_LF, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
                 o_update<LPC, CPL>(P, gl, active, m, t, TAG_O2, c1, c2s, u);
             } else {
                 // App. F step 2: u uniform on the sphere
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 const uint32_t t0 = (uint32_t)H.t;
                 for (int n = 0; n < P.N; ++n) {
                     o_update<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O1, c1, c2s, u);
-                    phi_step<KIND, LPC, CPL>(P, CF, H.integ, eps, gl, lane, y, u, g, lp, dl, pr, sg);
+                    phi_step<KIND, LPC, CPL>(P, CF, H.integ, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
                     o_update<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O2, c1, c2s, u);
                 }
             }

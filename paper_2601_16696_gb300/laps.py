@@ -64,7 +64,7 @@ class Config(C.Structure):
                 ("precision", C.c_int), ("barrier_timeout_ns", C.c_int64),
                 ("chains_per_block", C.c_int), ("lanes_per_chain", C.c_int),
                 ("coords_per_lane", C.c_int), ("barrier_extra_arrivals", C.c_int),
-                ("dtilde_K", C.c_int)]
+                ("dtilde_K", C.c_int), ("dense_streamed", C.c_int)]
 
 
 class Stats(C.Structure):

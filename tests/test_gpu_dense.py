@@ -1,7 +1,9 @@
 """GPU parity of the dense-precision Gaussian (the randomly oriented
-ill-conditioned Gaussian of the paper's Sec. 6), sampled on the streamed path
-with its gradient -P x as one chains-by-coordinates contraction, against the
-FP64 oracle on the same binary32-rounded precision matrix.
+ill-conditioned Gaussian of the paper's Sec. 6), sampled in the register-resident
+kernel (P in shared memory, one matrix-vector product per chain) for d <= 128
+and on the streamed path (its gradient -P x one chains-by-coordinates
+contraction) beyond, both against the FP64 oracle on the same binary32-rounded
+precision matrix; the run-level tests cover both paths.
 
 The target is ill-conditioned (condition number 1.1e5), so -P x cancels and a
 binary32 dot product is off by ~1e-4 of max|g|; the kernel accumulates the
@@ -66,10 +68,15 @@ def test_dense_logp_grad(L, ora, d, M):
         np.testing.assert_allclose(lp.double().cpu().numpy(), lp_o, rtol=1e-6)
 
 
-def test_dense_first_ten_steps_fixed_step(L, ora):
+PATHS = [pytest.param(0, id="resident"), pytest.param(1, id="streamed")]
+
+
+@pytest.mark.parametrize("streamed", PATHS)
+def test_dense_first_ten_steps_fixed_step(L, ora, streamed):
     """Full size (d = 100, M = 4096, condition number 1.1e5), step size held fixed."""
     pr = W.icg()
-    s = _gpu(L, pr, seed=3, fixed_eps=0.002)
+    s = _gpu(L, pr, seed=3, fixed_eps=0.002, dense_streamed=streamed)
+    assert s.launch_info()["resident"] == 1 - streamed
     r = _ora(ora, pr, seed=3, fixed_eps=0.002)
     np.testing.assert_array_equal(s.sample().double().cpu().numpy(), pr.x0)
     for k in range(10):
@@ -82,11 +89,12 @@ def test_dense_first_ten_steps_fixed_step(L, ora):
         assert a["L"] == pytest.approx(b["L"], rel=1e-5)
 
 
-def test_dense_first_ten_steps_adaptive(L, ora):
+@pytest.mark.parametrize("streamed", PATHS)
+def test_dense_first_ten_steps_adaptive(L, ora, streamed):
     """Paper defaults: the bar is 3x the oracle's own divergence from its run
     with a binary32 state (see tests/test_gpu_parity.py), never below 1e-5."""
     pr = W.icg(M=1024)
-    s = _gpu(L, pr, seed=3)
+    s = _gpu(L, pr, seed=3, dense_streamed=streamed)
     r = _ora(ora, pr, seed=3)
     r32 = _ora(ora, pr, seed=3, round_state_f32=1)
     for k in range(10):
@@ -104,11 +112,12 @@ def _tail(trace, key, phase):
     return float(np.mean([x[key] for x in rows[len(rows) // 2:]]))
 
 
-def test_dense_final_b2_within_10_percent(L, ora):
+@pytest.mark.parametrize("streamed", PATHS)
+def test_dense_final_b2_within_10_percent(L, ora, streamed):
     """Whole unswitched run, M = 1024, 2000 steps (oracle seed-to-seed spread of
     the b^2_avg tail mean 2%); b^2_max falls below 0.01 after ~630 gradients."""
     pr = W.icg(M=1024, n_steps=2000)
-    s = _gpu(L, pr, seed=0)
+    s = _gpu(L, pr, seed=0, dense_streamed=streamed)
     s.run()
     st = s.stats()
     r = _ora(ora, pr, seed=0)
@@ -118,7 +127,8 @@ def test_dense_final_b2_within_10_percent(L, ora):
     assert abs(bg - bo) <= 0.10 * bo, (bg, bo)
 
 
-def test_dense_switched_run(L, ora):
+@pytest.mark.parametrize("streamed", PATHS)
+def test_dense_switched_run(L, ora, streamed):
     """Switch forced at step 400: the diagonal preconditioner cannot undo the
     rotation, so MAMS is still removing bias at the end and its b^2 depends on
     the path (oracle, 5 seeds: b^2_avg tail mean 0.0044-0.0062).  The step
@@ -129,7 +139,7 @@ def test_dense_switched_run(L, ora):
     seed spread."""
     pr = W.icg(M=1024, n_steps=2000)
     cfg = {"force_switch_at": 400}
-    s = _gpu(L, pr, seed=0, **cfg)
+    s = _gpu(L, pr, seed=0, dense_streamed=streamed, **cfg)
     s.run()
     st = s.stats()
     r = _ora(ora, pr, seed=0, **cfg)
@@ -144,18 +154,38 @@ def test_dense_switched_run(L, ora):
     assert abs(bg - bo) <= 0.35 * bo, (bg, bo)
 
 
-def test_dense_determinism_and_checkpoint(L):
+@pytest.mark.parametrize("streamed", PATHS)
+def test_dense_determinism_and_checkpoint(L, streamed):
     pr = W.icg(d=40, M=200, n_steps=300)
-    a = _gpu(L, pr, seed=4, force_switch_at=100)
+    a = _gpu(L, pr, seed=4, force_switch_at=100, dense_streamed=streamed)
     a.step(150)
-    b = _gpu(L, pr, seed=4, force_switch_at=100)
+    b = _gpu(L, pr, seed=4, force_switch_at=100, dense_streamed=streamed)
     b.step(90)
     blob = b.checkpoint()
-    c = _gpu(L, pr, seed=99, force_switch_at=100)
+    c = _gpu(L, pr, seed=99, force_switch_at=100, dense_streamed=streamed)
     c.restore(blob)
     c.step(60)
     np.testing.assert_array_equal(a.sample().cpu().numpy(), c.sample().cpu().numpy())
     assert a.stats()["eps"] == c.stats()["eps"]
+
+
+def test_dense_path_by_dimension(L, ora):
+    """d <= 128 runs in the register-resident kernel, larger d on the streamed
+    path; the larger case's first steps against the oracle."""
+    pr = W.icg(d=150, M=256, n_steps=50)
+    s = _gpu(L, pr, seed=2, fixed_eps=0.002)
+    assert s.launch_info()["resident"] == 0
+    r = _ora(ora, pr, seed=2, fixed_eps=0.002)
+    s.step(5)
+    r.iterate(5)
+    assert _rel(s.sample().double().cpu().numpy(), r.x()) <= 1e-5
+    small = W.icg(d=37, M=65, n_steps=50)
+    s = _gpu(L, small, seed=2, fixed_eps=0.002)
+    assert s.launch_info()["resident"] == 1
+    r = _ora(ora, small, seed=2, fixed_eps=0.002)
+    s.step(5)
+    r.iterate(5)
+    assert _rel(s.sample().double().cpu().numpy(), r.x()) <= 1e-5
 
 
 def test_dense_rejected_where_not_built(L):
