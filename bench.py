@@ -294,23 +294,29 @@ def _forms(flush, stream, mhz, seed0):
         tg.logp_grad(x0)
     reps = 20
     gms = timed_ms(lambda: [tg.logp_grad(x0) for _ in range(reps)]) / reps
-    s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, stop_b2_max=1)  # b2_first on b^2_max
-    s.set_truth(pr.Ex2, pr.Varx2)
-    s.init(x0, seed=seed0)
-    s.step(3)
-    run_ms = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
+    runs = {}
+    for streamed in (1, 0):  # the streamed path, then the default (register-resident at d = 100)
+        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, stop_b2_max=1,  # b2_first on b^2_max
+                         dense_streamed=streamed)
+        s.set_truth(pr.Ex2, pr.Varx2)
+        s.init(x0, seed=seed0)
+        s.step(3)
+        runs[streamed] = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
+    run_ms = runs[0]
     st = s.stats()
     flops = 2.0 * pr.M * pr.d * pr.d  # the contraction -P x of every chain, per gradient
     achieved = flops / (gms * 1e-3) / 1e12
     out["icg"] = {
         "workload": "icg_d%d_M%d_%dsteps (cond %.2g)" % (pr.d, pr.M, pr.n_steps, pr.extra["cond"]),
         "value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT, "run_ms": run_ms,
+        "path": "register-resident" if s.launch_info()["resident"] else "streamed",
+        "run_ms_streamed_path": runs[1],
         "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
         "time_to_b2_ms": st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None,
         "grads_to_b2": st["b2_first_grads"] if st["b2_first_t"] >= 0 else None, "b2": "b2_max",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "gauss_dense_grad_kernel<4,4>",
+                     "kernel": "gauss_dense_grad_kernel<4,2> (the streamed path's gradient)",
                      "timed": "laps_target_logp_grad (points packed, contraction, partials "
                               "unpacked), %.3f ms per call; 2 M d^2 algorithmic FLOP, the "
                               "compensated accumulation's extra operations not counted" % gms,
