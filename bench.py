@@ -225,7 +225,9 @@ def _forms(flush, stream, mhz, seed0):
     lr = {"workload": "logreg_d%d_n%d_M%d_%dsteps" % (pr.d, n, pr.M, pr.n_steps),
           "b2": "b2_max", "truth": "Laplace approximation of the posterior (FP64)",
           "switch": "paper rule (max delta < 0.01)"}
-    for name, prec in (("mixed", 1), ("fp32", 0)):
+    kernels = {0: "logreg_grad_f32_kernel<128>", 1: "logreg_grad_mma_kernel<128>",
+               2: "logreg_grad_x3_kernel<128>"}
+    for name, prec in (("mixed", 1), ("fp32", 0), ("bf16x3", 2)):
         for _ in range(3):
             tg.logp_grad(x0, precision=prec)
         reps = 10
@@ -239,22 +241,42 @@ def _forms(flush, stream, mhz, seed0):
         run_ms = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
         st = s.stats()
         achieved = flops / (gms * 1e-3) / 1e12
-        peak = pk["bf16_tflops"] if prec == 1 else fp32_peak
+        # the three-term form runs six BF16 products per FP32-accurate product
+        peak = {0: fp32_peak, 1: pk["bf16_tflops"], 2: pk["bf16_tflops"] / 6.0}[prec]
         lr[name] = {
             "value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT,
             "run_ms": run_ms, "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
             "time_to_b2_ms": st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None,
             "b2_max_final": st["b2_max"],
-            "roofline": {"bound": "tensor" if prec == 1 else "alu", "achieved": achieved,
+            "roofline": {"bound": "alu" if prec == 0 else "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None,
-                         "kernel": "logreg_grad_mma_kernel<128>" if prec == 1
-                         else "logreg_grad_f32_kernel<128>",
+                         "traffic": None, "kernel": kernels[prec],
                          "timed": "laps_target_logp_grad_prec (points packed, contraction, "
                                   "partials summed), %.3f ms per call" % gms,
-                         "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)" if prec == 1
-                         else "%d SMs x 128 FP32 FMA lanes x 2 x %.0f MHz" % (nsm, mhz)}}
+                         "peak_basis": {0: "%d SMs x 128 FP32 FMA lanes x 2 x %.0f MHz" % (nsm, mhz),
+                                        1: "measured bf16 burst (MEASURED_PEAKS.json)",
+                                        2: "measured bf16 burst / 6 (six BF16 products per "
+                                           "FP32-accurate product)"}[prec]}}
     out["logreg"] = lr
+    # ---- the logistic regression's adjusted phase: the switch forced after 100
+    # unadjusted steps (the paper's rule does not fire on this workload), then
+    # MAMS proposals to the end of the run; the adjusted phase's contraction on
+    # the CUDA cores (mixed) or on the tensor cores at FP32 accuracy
+    adj = {"workload": "logreg_d%d_n%d_M%d_%dsteps, switch forced at step 100" % (pr.d, n, pr.M, pr.n_steps)}
+    for name, prec in (("mixed", 1), ("mixed_bf16x3", 3)):
+        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, precision=prec, force_switch_at=100)
+        s.set_truth(pr.Ex2, pr.Varx2)
+        s.init(x0, seed=seed0)
+        s.step(3)
+        run_ms = timed_ms(lambda: (s.init(x0, seed=seed0 + 1), s.run()))
+        st = s.stats()
+        tail = [r["acc"] for r in s.trace() if r["phase"] == 1 and not r["adapting"]]
+        adj[name] = {"value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT, "run_ms": run_ms,
+                     "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
+                     "acceptance": float(statistics.mean(tail)) if tail else None,
+                     "b2_max_final": st["b2_max"]}
+    tg.check()
+    out["logreg_adjusted"] = adj
     # ---- the batch
     probs = workloads.batch64()
     coords = sum(p.d * p.M for p in probs)
@@ -338,7 +360,8 @@ def _forms(flush, stream, mhz, seed0):
 def ncu_case_form(which: str):
     """No timing: small cases of the other kernels, for ncu captures (a few hundred
     MB on the device at most).  logreg: the mixed-precision run of the logistic
-    regression, tcgen05 gradient launches 1 (init) to 4; batch: 32 problems of the
+    regression, tcgen05 gradient launches 1 (init) to 4; logreg_x3: the same with
+    the three-term split form (LAPS_BF16X3); batch: 32 problems of the
     batch (d < 10^4, 33 M coordinates), batch_kernel launch 1 (init), 2 and 3 (5
     unadjusted iterations each); dense: the ill-conditioned Gaussian, gradient
     launches 1 (init) to 4."""
@@ -346,9 +369,10 @@ def ncu_case_form(which: str):
     from paper_2601_16696_gb300 import build, laps, workloads
     build.build()
     info = {"ncu_case": which}
-    if which == "logreg":
+    if which in ("logreg", "logreg_x3"):
         pr = workloads.logreg()
-        s = laps.Sampler(laps.Target.from_problem(pr), pr.M, n_total_steps=pr.n_steps, precision=1)
+        s = laps.Sampler(laps.Target.from_problem(pr), pr.M, n_total_steps=pr.n_steps,
+                         precision=1 if which == "logreg" else 2)
         s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)
         s.step(3)
     elif which == "batch":
@@ -455,7 +479,7 @@ def main():
                          "iterations after two others (the case profiled under ncu)")
     ap.add_argument("--ncu-case-adjusted", action="store_true",
                     help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
-    ap.add_argument("--ncu-case-form", choices=["logreg", "batch", "dense"],
+    ap.add_argument("--ncu-case-form", choices=["logreg", "logreg_x3", "batch", "dense"],
                     help="no timing: a small case of another kernel (for ncu)")
     ap.add_argument("--ablations", action="store_true",
                     help="no contract line: the paper's ablations (MAMS only, fixed step, "

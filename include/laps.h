@@ -75,10 +75,16 @@ typedef enum {
 typedef int (*laps_logp_grad_fn)(const float* x, int64_t M, int64_t ld, float* logp, float* grad,
                                  void* stream, void* user_data);
 
-/* Arithmetic of the logistic-regression contraction in the unadjusted phase. */
+/* Arithmetic of the logistic-regression contraction in each phase.  The
+   tensor-core forms are built for d <= 128. */
 typedef enum {
-    LAPS_FP32 = 0,   /* FP32 everywhere */
-    LAPS_MIXED = 1   /* BF16 tensor-core contraction (FP32 accumulate) while unadjusted */
+    LAPS_FP32 = 0,          /* FP32 on the CUDA cores in both phases */
+    LAPS_MIXED = 1,         /* BF16 tensor-core contraction (FP32 accumulate) while unadjusted,
+                               FP32 on the CUDA cores once adjusted */
+    LAPS_BF16X3 = 2,        /* tensor cores at FP32 accuracy in both phases: every operand as
+                               three BF16 terms, the six cross products of order >= 2^-16 */
+    LAPS_MIXED_BF16X3 = 3   /* BF16 tensor-core contraction while unadjusted, the three-term
+                               form of LAPS_BF16X3 once adjusted */
 } laps_precision;
 
 typedef struct {
@@ -187,8 +193,11 @@ laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t
 /* The same in a given arithmetic: LAPS_FP32 is laps_target_logp_grad;
  * LAPS_MIXED (LOGREG with d <= 128) is the tensor-core form the sampler's
  * unadjusted phase uses: the target on the BF16-rounded data, each point as a
- * sum of two BF16 terms, residuals y - sigmoid(z) in BF16, FP32 accumulation.
- * Stream-ordered; a bounded device wait that expired is latched in the
+ * sum of two BF16 terms, residuals y - sigmoid(z) in BF16, FP32 accumulation;
+ * LAPS_BF16X3 (LOGREG with d <= 128) is the tensor-core form at FP32
+ * accuracy: points, data and residuals each as three BF16 terms, the six
+ * cross products of order >= 2^-16, FP32 accumulation, the FP32 epilogue of
+ * laps_target_logp_grad.  Stream-ordered; a bounded device wait that expired is latched in the
  * target's status word, which laps_target_status returns. */
 laps_status laps_target_logp_grad_prec(const laps_target* tg, const float* x, int64_t M,
                                        float* logp, float* grad, int precision, void* stream);

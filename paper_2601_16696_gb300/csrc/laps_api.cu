@@ -394,6 +394,12 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out) 
             if (L.Xtb) cudaFree(L.Xtb);
             L.Xb = L.Xtb = nullptr;
         }
+        // the three-term split of X for the tensor-core form at FP32 accuracy
+        if (logreg_x3_supported(L.kp) && logreg_x3_prepare(L) != cudaSuccess) {
+            cudaGetLastError();
+            if (L.X3b) cudaFree(L.X3b);
+            L.X3b = nullptr;
+        }
         if (cudaMalloc(&t->status, sizeof(int)) != cudaSuccess ||
             cudaMemset(t->status, 0, sizeof(int)) != cudaSuccess) {
             laps_target_destroy(t);
@@ -412,6 +418,7 @@ void laps_target_destroy(laps_target* t) {
     if (t->lr.y) cudaFree(t->lr.y);
     if (t->lr.Xb) cudaFree(t->lr.Xb);
     if (t->lr.Xtb) cudaFree(t->lr.Xtb);
+    if (t->lr.X3b) cudaFree(t->lr.X3b);
     if (t->status) cudaFree(t->status);
     delete t;
 }
@@ -429,6 +436,8 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
                           !(tg->kind == TGT_GAUSS_DENSE && tg->d_pad <= kDenseResidentMax && !cfg->dense_streamed);
     if (cfg->dtilde_K > 0 && (streamed || tg->kind == TGT_GAUSS_DENSE))
         return fail(LAPS_ERR_UNSUPPORTED, "the full-rank bias proxy is built for the diagonal, banana and funnel targets");
+    if ((int)cfg->precision < LAPS_FP32 || (int)cfg->precision > LAPS_MIXED_BF16X3)
+        return fail(LAPS_ERR_INVALID_ARG, "unknown precision");
     if (cfg->precision != LAPS_FP32 && tg->kind != TGT_LOGREG)
         return fail(LAPS_ERR_UNSUPPORTED, "mixed precision applies to LOGREG targets only");
     laps_ctx* c = new laps_ctx();

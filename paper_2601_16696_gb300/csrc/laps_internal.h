@@ -59,12 +59,15 @@ struct laps_ctx {
     size_t seg_smem = 0, fin_slice_smem = 0, fin_gather_smem = 0;
     laps::Hyper* h_hyper = nullptr;  // pinned host copy of the phase machine (owned)
     laps::Coefs cf{};                // integrator tables on the host
-    // mixed precision: BF16 tensor-core gradient while unadjusted
+    // contraction form of each phase (GF_*); mixed: the unadjusted one is
+    // the BF16 tensor-core form, which reads the hi | lo copy Wb
+    int gf_unadj = 0, gf_adj = 0;
     bool mixed = false;
     bool refreshed = false;          // streamed: the switch's one-time work is done
     void* Wb = nullptr;              // [M_pad][2 d_pad] BF16 hi | lo copy of the points
     int64_t M_pad = 0;
     int nsplit_mma = 1, rps_mma = 64;
+    int nsplit_x3 = 1, rps_x3 = 64;   // the three-term tensor-core form's data splits
     alignas(64) unsigned char tmW[128];  // CUtensorMap of Wb
 };
 
@@ -94,6 +97,9 @@ laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStre
 laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st);
 // dense-precision Gaussian (laps_gauss_dense.cu): G = -W P, LP = -1/2 sum W (P W)
 constexpr int kDenseMaxDim = 512;
+// forms of the logistic-regression contraction: FP32 on the CUDA cores, BF16
+// tensor cores, tensor cores at FP32 accuracy (three-term BF16 split)
+enum GradForm : int { GF_F32 = 0, GF_BF16 = 1, GF_X3 = 2 };
 cudaError_t gauss_dense_grad(const float* P, int d_pad, int d, const float* W, int64_t M, float* G,
                              float2* LP, cudaStream_t st);
 inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_GAUSS_DENSE || kind == TGT_USER; }

@@ -26,6 +26,9 @@ struct LogregData {
     void* Xtb;        // [kp][n_pad] BF16 (X transposed)
     alignas(64) unsigned char tmX[128];   // CUtensorMap of Xb
     alignas(64) unsigned char tmXt[128];  // CUtensorMap of Xtb
+    // FP32-accurate tensor-core form: the three BF16 terms of X, [3][n_pad][kp]
+    void* X3b;
+    alignas(64) unsigned char tmX3[128];  // CUtensorMap of X3b
 };
 
 // Largest padded dimension the gradient kernels take.
@@ -47,6 +50,18 @@ cudaError_t logreg_pack_points(const float* x, int64_t M, int d, int kp, float* 
 cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W32, int64_t M, int S,
                             int rps, float* gpart, float2* lpart, int* status, long long timeout_ns,
                             cudaStream_t st);
+
+// ---- tensor-core gradient at FP32 accuracy (three-term BF16 split): laps_logreg_x3.cu
+bool logreg_x3_supported(int kp);
+// the split copy of X and its tensor map (allocates X3b; synchronises)
+cudaError_t logreg_x3_prepare(LogregData& D);
+size_t logreg_x3_smem(int kp);
+// data splits of the launch (every split non-empty) and rows per split
+int logreg_x3_splits(const LogregData& D, int64_t M, int nsm, int* rps);
+// gradient partials like logreg_grad_f32 from the FP32 points W32 [M][kp], the
+// data split by logreg_x3_splits; a bounded wait that expires sets *status
+cudaError_t logreg_grad_x3(const LogregData& D, const float* W32, int64_t M, int S, int rps, float* gpart,
+                           float2* lpart, int* status, long long timeout_ns, cudaStream_t st);
 
 // log p and gradient at the M points W [M][kp] (x-space, padding columns 0),
 // with the data split into S row ranges: gpart [S][M][kp] and lpart [S][M]

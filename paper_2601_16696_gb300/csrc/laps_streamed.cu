@@ -401,21 +401,32 @@ laps_status launch_seg(laps_ctx* c, const KParams& P, const SegOp& op, cudaStrea
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "seg_kernel");
 }
 
-// the gradient of the working points; mma: the BF16 tensor-core form (mixed
-// precision, unadjusted phase), else FP32
-laps_status launch_grad(laps_ctx* c, bool mma, cudaStream_t st) {
+// the gradient of the working points in contraction form `form` (GF_*; the
+// dense Gaussian and user targets have one form)
+laps_status launch_grad(laps_ctx* c, int form, cudaStream_t st) {
     cudaError_t e;
     if (c->tg->kind == TGT_GAUSS_DENSE) {
         e = gauss_dense_grad(c->tg->prec_dense, c->d_pad, c->d, c->W, c->M, c->gpart, c->lpart, st);
         return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
     }
     if (c->tg->kind == TGT_USER) return user_grad(c->tg, c->W, c->M, c->d_pad, c->gpart, c->ulp, c->lpart, st);
-    if (mma)
+    if (form == GF_BF16)
         e = logreg_grad_mma(c->tg->lr, c->tmW, c->W, c->M, c->nsplit_mma, c->rps_mma, c->gpart, c->lpart,
                             c->status, c->cfg.barrier_timeout_ns, st);
+    else if (form == GF_X3)
+        e = logreg_grad_x3(c->tg->lr, c->W, c->M, c->nsplit_x3, c->rps_x3, c->gpart, c->lpart, c->status,
+                           c->cfg.barrier_timeout_ns, st);
     else
         e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st);
-    return e == cudaSuccess ? LAPS_OK : cuda_fail(e, mma ? "logreg gradient (tensor cores)" : "logreg gradient");
+    return e == cudaSuccess ? LAPS_OK
+                            : cuda_fail(e, form == GF_BF16 ? "logreg gradient (tensor cores)"
+                                           : form == GF_X3 ? "logreg gradient (tensor cores, three-term split)"
+                                                           : "logreg gradient");
+}
+
+// data splits (gradient partials) the given form writes
+int nsplit_of(const laps_ctx* c, int form) {
+    return form == GF_BF16 ? c->nsplit_mma : form == GF_X3 ? c->nsplit_x3 : c->nsplit;
 }
 
 laps_status launch_fin(laps_ctx* c, const KParams& P, cudaStream_t st) {
@@ -443,16 +454,16 @@ SegOp seg_op(int phase) {
 laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
     KParams P;
     fill_params(c, 1, nullptr, 0.0f, P);
+    P.nsplit = nsplit_of(c, phase == 0 ? c->gf_unadj : c->gf_adj);
     if (phase == 0) {
         // O_{eps/2} B_{eps/2} A_eps [grad] B_{eps/2} O_{eps/2}  (leapfrog, App. E)
-        if (c->mixed) P.nsplit = c->nsplit_mma;
         SegOp a = seg_op(0);
         a.first = 1;
         a.o1_step = 0;
         a.bB = c->cf.b[INTEG_LF][0];
         a.a = c->cf.a[INTEG_LF][0];
         LCK(launch_seg(c, P, a, st));
-        LCK(launch_grad(c, c->mixed, st));
+        LCK(launch_grad(c, c->gf_unadj, st));
         SegOp b = seg_op(0);
         b.after_grad = 1;
         b.bA = c->cf.b[INTEG_LF][1];
@@ -472,14 +483,14 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
     LCK(launch_seg(c, P, a, st));
     for (int n = 0; n < N; ++n) {
         for (int s = 1; s < K - 1; ++s) {
-            LCK(launch_grad(c, false, st));
+            LCK(launch_grad(c, c->gf_adj, st));
             SegOp m = seg_op(1);
             m.after_grad = 1;
             m.bA = c->cf.b[I][s];
             m.a = c->cf.a[I][s];
             LCK(launch_seg(c, P, m, st));
         }
-        LCK(launch_grad(c, false, st));
+        LCK(launch_grad(c, c->gf_adj, st));
         SegOp e = seg_op(1);
         e.after_grad = 1;
         e.bA = c->cf.b[I][K - 1];
@@ -534,19 +545,24 @@ laps_status streamed_setup(laps_ctx* c) {
     if (c->tg->kind != TGT_LOGREG) c->nsplit = 1;  // one evaluation writes every coordinate of its chains
     c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
     coefs_table(c->cf);
-    if (c->cfg.precision == LAPS_MIXED) {
-        if (!logreg_mma_supported(dp) || c->tg->lr.Xb == nullptr)
-            return fail(LAPS_ERR_UNSUPPORTED, "mixed precision is built for LOGREG with d <= 128");
-        c->mixed = true;
-        c->M_pad = (c->M + 127) / 128 * 128;
-        c->nsplit_mma = logreg_mma_splits(c->tg->lr, c->M, nsm, &c->rps_mma);
-    }
+    const int pr = (int)c->cfg.precision;
+    c->gf_unadj = pr == LAPS_MIXED || pr == LAPS_MIXED_BF16X3 ? GF_BF16 : pr == LAPS_BF16X3 ? GF_X3 : GF_F32;
+    c->gf_adj = pr == LAPS_BF16X3 || pr == LAPS_MIXED_BF16X3 ? GF_X3 : GF_F32;
+    if (c->gf_unadj == GF_BF16 && (!logreg_mma_supported(dp) || c->tg->lr.Xb == nullptr))
+        return fail(LAPS_ERR_UNSUPPORTED, "mixed precision is built for LOGREG with d <= 128");
+    if (c->gf_adj == GF_X3 && (!logreg_x3_supported(dp) || c->tg->lr.X3b == nullptr))
+        return fail(LAPS_ERR_UNSUPPORTED, "the three-term tensor-core form is built for LOGREG with d <= 128");
+    c->mixed = c->gf_unadj == GF_BF16;
+    if (c->gf_unadj == GF_BF16) c->nsplit_mma = logreg_mma_splits(c->tg->lr, c->M, nsm, &c->rps_mma);
+    if (c->gf_unadj == GF_X3 || c->gf_adj == GF_X3)
+        c->nsplit_x3 = logreg_x3_splits(c->tg->lr, c->M, nsm, &c->rps_x3);
+    if (c->mixed) c->M_pad = (c->M + 127) / 128 * 128;
     return LAPS_OK;
 }
 
 laps_status streamed_alloc(laps_ctx* c) {
     const size_t Md = (size_t)c->M * c->d_pad;
-    const int S = std::max(c->nsplit, c->mixed ? c->nsplit_mma : 1);
+    const int S = std::max({c->nsplit, c->nsplit_mma, c->nsplit_x3});
     auto alloc = [&](void** p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) return false;
         c->allocs.push_back(*p);
@@ -573,15 +589,16 @@ laps_status streamed_alloc(laps_ctx* c) {
 
 namespace {
 // after the switch of a mixed-precision run: the accepted g and log p again in
-// FP32 (the unadjusted phase computed them on the BF16 data), so that every
-// Metropolis test compares log p of one arithmetic
-laps_status reevaluate_fp32(laps_ctx* c, cudaStream_t st) {
+// the adjusted phase's arithmetic (the unadjusted phase computed them on the
+// BF16 data), so that every Metropolis test compares log p of one arithmetic
+laps_status reevaluate_adjusted(laps_ctx* c, cudaStream_t st) {
     KParams P;
     fill_params(c, 1, nullptr, 0.0f, P);
+    P.nsplit = nsplit_of(c, c->gf_adj);
     SegOp a = seg_op(1);
     a.init = 3;
     LCK(launch_seg(c, P, a, st));
-    LCK(launch_grad(c, false, st));
+    LCK(launch_grad(c, c->gf_adj, st));
     SegOp b = seg_op(1);
     b.init = 4;
     LCK(launch_seg(c, P, b, st));
@@ -590,8 +607,8 @@ laps_status reevaluate_fp32(laps_ctx* c, cudaStream_t st) {
 
 // the one-time work of the switch, enqueued by the host once it reads the new
 // phase (the iterations enqueued after the switching one are empty): the
-// accepted state into preconditioned coordinates, then, for the mixed form,
-// its g and log p again in FP32
+// accepted state into preconditioned coordinates, then, for the mixed forms,
+// its g and log p again in the adjusted phase's arithmetic
 laps_status after_switch(laps_ctx* c, cudaStream_t st) {
     KParams P;
     fill_params(c, 1, nullptr, 0.0f, P);
@@ -599,7 +616,7 @@ laps_status after_switch(laps_ctx* c, cudaStream_t st) {
     precondition_kernel<<<blocks, 256, 0, st>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "precondition_kernel");
-    if (c->mixed) LCK(reevaluate_fp32(c, st));
+    if (c->gf_unadj != c->gf_adj) LCK(reevaluate_adjusted(c, st));
     c->refreshed = true;
     return LAPS_OK;
 }
@@ -608,12 +625,12 @@ laps_status after_switch(laps_ctx* c, cudaStream_t st) {
 laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st) {
     KParams P;
     fill_params(c, 0, x0, x0_scale, P);
-    if (c->mixed) P.nsplit = c->nsplit_mma;
+    P.nsplit = nsplit_of(c, c->gf_unadj);
     SegOp a = seg_op(0);
     a.first = 1;
     a.init = 1;
     LCK(launch_seg(c, P, a, st));
-    LCK(launch_grad(c, c->mixed, st));
+    LCK(launch_grad(c, c->gf_unadj, st));
     SegOp b = seg_op(0);
     b.init = 2;
     LCK(launch_seg(c, P, b, st));

@@ -184,6 +184,41 @@ static laps_status logreg_logp_grad_mixed(const laps_target* tg, const float* x,
     return LAPS_OK;
 }
 
+// LOGREG on the tensor cores at FP32 accuracy (points, data and residuals
+// each as three BF16 terms); stream-ordered, a bounded wait that expired is
+// latched in the target's status word
+static laps_status logreg_logp_grad_x3(const laps_target* tg, const float* x, int64_t M, float* logp,
+                                       float* grad, cudaStream_t st) {
+    const LogregData& L = tg->lr;
+    if (!L.X3b) return fail(LAPS_ERR_UNSUPPORTED, "the three-term tensor-core form is built for LOGREG with d <= 128");
+    const int kp = L.kp, d = tg->d;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int rps = 64;
+    const int S = logreg_x3_splits(L, M, nsm, &rps);
+    float *W32 = nullptr, *G = nullptr;
+    float2* lp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&W32, (size_t)M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G, (size_t)S * M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&lp, (size_t)S * M * 8, st);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((M * kp + 255) / 256, 4096));
+    if (e == cudaSuccess) {
+        logreg_pack_kernel<<<blocks, 256, 0, st>>>(x, W32, M, d, kp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = logreg_grad_x3(L, W32, M, S, rps, G, lp, tg->status, 2000000000LL, st);
+    if (e == cudaSuccess) {
+        logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp, S);
+        e = cudaGetLastError();
+    }
+    if (W32) cudaFreeAsync(W32, st);
+    if (G) cudaFreeAsync(G, st);
+    if (lp) cudaFreeAsync(lp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "LOGREG logp_grad (tensor cores, three-term split)");
+    return LAPS_OK;
+}
+
 }  // namespace laps
 
 using namespace laps;
@@ -203,9 +238,10 @@ extern "C" laps_status laps_target_logp_grad_prec(const laps_target* tg, const f
                                                   float* logp, float* grad, int precision, void* stream) {
     if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (precision == LAPS_FP32) return laps_target_logp_grad(tg, x, M, logp, grad, stream);
-    if (precision != LAPS_MIXED) return fail(LAPS_ERR_INVALID_ARG, "unknown precision");
+    if (precision != LAPS_MIXED && precision != LAPS_BF16X3) return fail(LAPS_ERR_INVALID_ARG, "unknown precision");
     if (tg->kind != TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "mixed precision applies to LOGREG only");
     if (M == 0) return LAPS_OK;
+    if (precision == LAPS_BF16X3) return logreg_logp_grad_x3(tg, x, M, logp, grad, (cudaStream_t)stream);
     return logreg_logp_grad_mixed(tg, x, M, logp, grad, (cudaStream_t)stream);
 }
 

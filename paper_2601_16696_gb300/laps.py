@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblaps.so")
 
 GAUSS_DIAG, BANANA, FUNNEL, LOGREG, GAUSS_DENSE, USER = 0, 1, 2, 3, 4, 5
-FP32, MIXED = 0, 1
+FP32, MIXED, BF16X3, MIXED_BF16X3 = 0, 1, 2, 3
 LF, MN2, MN4 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "NONFINITE",
           6: "UNSUPPORTED"}
@@ -272,7 +272,8 @@ class Target:
 
     def logp_grad(self, x: torch.Tensor, precision: int = 0, stream=None):
         """log p [M] and grad log p [M, d] of the rows of x (FP32, CUDA);
-        precision 1 (LAPS_MIXED): the tensor-core form of a LOGREG target."""
+        precision 1 (LAPS_MIXED): the BF16 tensor-core form of a LOGREG target;
+        2 (LAPS_BF16X3): its tensor-core form at FP32 accuracy."""
         x = x.contiguous()
         M = x.shape[0]
         logp = torch.empty(M, dtype=torch.float32, device=x.device)
