@@ -235,19 +235,31 @@ __device__ __forceinline__ ff a_step(const KParams& P, int gl, int lane, float* 
 // ---------------------------------------------------------------- O, B, A maps
 // App. E, Eq. "O update": u <- (c1 u + c2 Z) / |.|, Z ~ N(0, I/d) per coordinate
 // (std 1/sqrt(d)); c2s = c2 / sqrt(d).
+// The noise Z of one O map (this lane's coordinate blocks), apart from the map
+// itself: it depends only on the counters, so a step can draw both of its O
+// maps' noise up front and the generator's arithmetic overlaps the reductions.
 template <int LPC, int CPL>
-__device__ __forceinline__ void o_update(const KParams& P, int gl, bool active, uint32_t m,
-                                         uint32_t t, uint32_t tag, float c1, float c2s,
-                                         float (&u)[CPL]) {
+__device__ __forceinline__ void o_noise(const KParams& P, int gl, bool active, uint32_t m, uint32_t t,
+                                        uint32_t tag, float (&z)[CPL]) {
+#pragma unroll
+    for (int k = 0; k < CPL / 4; ++k) {
+        const int j = gl + LPC * k;
+        float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (active && j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) z[4 * k + c] = w[c];
+    }
+}
+template <int LPC, int CPL>
+__device__ __forceinline__ void o_apply(const KParams& P, int gl, float c1, float c2s, const float (&z)[CPL],
+                                        float (&u)[CPL]) {
     float n2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         const int j = gl + LPC * k;
-        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (active && j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, z);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[c]) : 0.0f;
+            const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[4 * k + c]) : 0.0f;
             u[4 * k + c] = v;
             n2 = fmaf(v, v, n2);
         }
@@ -256,6 +268,14 @@ __device__ __forceinline__ void o_update(const KParams& P, int gl, bool active, 
     const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
+}
+template <int LPC, int CPL>
+__device__ __forceinline__ void o_update(const KParams& P, int gl, bool active, uint32_t m,
+                                         uint32_t t, uint32_t tag, float c1, float c2s,
+                                         float (&u)[CPL]) {
+    float z[CPL];
+    o_noise<LPC, CPL>(P, gl, active, m, t, tag, z);
+    o_apply<LPC, CPL>(P, gl, c1, c2s, z, u);
 }
 
 // App. E, Eq. "B MCHMC" in the overflow-free form with zeta = e^-delta:
@@ -304,6 +324,26 @@ __device__ __forceinline__ void phi_step(const KParams& P, const Coefs& cf, int 
                                          const float (&sg)[CPL]) {
     const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
     const int K = cf.K[integ];
+    for (int k = 0; k < K; ++k) {
+        b_update<LPC, CPL>(cf.b[integ][k] * eps, inv_dm1, dm1, g, u, dl);
+        if (k < K - 1) {
+            const float ae = cf.a[integ][k] * eps;
+            const ff dlp = a_step<KIND, LPC, CPL>(P, gl, lane, dsm, ae, y, u, g, pr, sg);
+            dl = ff_add(dl, ff_neg(dlp));  // -log p(x') + log p(x)
+            lp = ff_add(lp, dlp);
+        }
+    }
+}
+
+// the same with the number of B maps known at compile time (LF: 2, MN2: 3), so
+// that the maps of one step are scheduled together
+template <int KIND, int LPC, int CPL, int K>
+__device__ __forceinline__ void phi_step_k(const KParams& P, const Coefs& cf, int integ, float eps,
+                                           int gl, int lane, float* dsm, float (&y)[CPL], float (&u)[CPL],
+                                           float (&g)[CPL], ff& lp, ff& dl, const float (&pr)[CPL],
+                                           const float (&sg)[CPL]) {
+    const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
+#pragma unroll
     for (int k = 0; k < K; ++k) {
         b_update<LPC, CPL>(cf.b[integ][k] * eps, inv_dm1, dm1, g, u, dl);
         if (k < K - 1) {

@@ -372,9 +372,12 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             ff dl = ff_make(0.0f);
             if (H.phase == 0) {
                 const uint32_t t = (uint32_t)H.t;
-                o_update<LPC, CPL>(P, gl, active, m, t, TAG_O1, c1, c2s, u);
-                phi_step<KIND, LPC, CPL>(P, CF, INTEG_LF, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
-                o_update<LPC, CPL>(P, gl, active, m, t, TAG_O2, c1, c2s, u);
+                float z1[CPL], z2[CPL];
+                o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O1, z1);
+                o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O2, z2);
+                o_apply<LPC, CPL>(P, gl, c1, c2s, z1, u);
+                phi_step_k<KIND, LPC, CPL, 2>(P, CF, INTEG_LF, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
+                o_apply<LPC, CPL>(P, gl, c1, c2s, z2, u);
             } else {
                 // App. F step 2: u uniform on the sphere
                 const uint32_t pidx = (uint32_t)H.p;
@@ -399,9 +402,16 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
                 // steps 3-4: N steps of phi with partial refreshes
                 const uint32_t t0 = (uint32_t)H.t;
                 for (int n = 0; n < P.N; ++n) {
-                    o_update<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O1, c1, c2s, u);
-                    phi_step<KIND, LPC, CPL>(P, CF, H.integ, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
-                    o_update<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O2, c1, c2s, u);
+                    float z1[CPL], z2[CPL];
+                    o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O1, z1);
+                    o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O2, z2);
+                    o_apply<LPC, CPL>(P, gl, c1, c2s, z1, u);
+                    if (H.integ == INTEG_MN2)
+                        phi_step_k<KIND, LPC, CPL, 3>(P, CF, INTEG_MN2, eps, gl, lane, dsm, y, u, g, lp, dl, pr,
+                                                      sg);
+                    else
+                        phi_step<KIND, LPC, CPL>(P, CF, H.integ, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
+                    o_apply<LPC, CPL>(P, gl, c1, c2s, z2, u);
                 }
             }
             // non-finite check over the chain's group
