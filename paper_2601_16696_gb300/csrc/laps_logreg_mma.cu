@@ -172,7 +172,7 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
         if (!ok) {
             atomicExch(&s_fail, 1);
             // wait (bounded) for the copies this thread issued
-            const unsigned long long d2 = global_ns() + (unsigned long long)A.timeout_ns;
+            const unsigned long long d2 = global_ns() + drain_ns(A.timeout_ns);
             mbar_wait(bar(B_WFULL), 0, d2);
             for (int c = max(0, issued - NSTAGE); c < issued; ++c)
                 mbar_wait(bar(B_XFULL + c % NSTAGE), (c / NSTAGE) & 1, d2);
@@ -228,7 +228,7 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
         } else {
             atomicExch(&s_fail, 1);
             tc_commit(bar(B_DRAIN));  // everything issued so far has completed once this arrives
-            mbar_wait(bar(B_DRAIN), 0, global_ns() + (unsigned long long)A.timeout_ns);
+            mbar_wait(bar(B_DRAIN), 0, global_ns() + drain_ns(A.timeout_ns));
         }
       }
       __syncwarp();

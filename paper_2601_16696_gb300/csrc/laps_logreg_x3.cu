@@ -217,7 +217,7 @@ logreg_grad_x3_kernel(const __grid_constant__ CUtensorMap tmX3, const X3Args A) 
         if (!ok) {
             atomicExch(&s_fail, 1);
             // wait (bounded) for the copies this thread issued
-            const unsigned long long d2 = global_ns() + (unsigned long long)A.timeout_ns;
+            const unsigned long long d2 = global_ns() + drain_ns(A.timeout_ns);
             for (int c = max(0, issued - NST); c < issued; ++c)
                 mbar_wait(bar(B::XFULL + c % NST), (c / NST) & 1, d2);
         }
@@ -285,7 +285,7 @@ logreg_grad_x3_kernel(const __grid_constant__ CUtensorMap tmX3, const X3Args A) 
         } else {
             atomicExch(&s_fail, 1);
             tc_commit(bar(B::DRAIN));  // everything issued so far has completed once this arrives
-            mbar_wait(bar(B::DRAIN), 0, global_ns() + (unsigned long long)A.timeout_ns);
+            mbar_wait(bar(B::DRAIN), 0, global_ns() + drain_ns(A.timeout_ns));
         }
       }
       __syncwarp();

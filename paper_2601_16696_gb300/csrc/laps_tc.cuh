@@ -44,6 +44,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
         if ((k & 63u) == 63u && global_ns() > deadline) return false;
     }
 }
+// Bound of the waits after a failure, for the copies and MMAs a CTA issued
+// itself: at least a second whatever the caller's timeout, so that a CTA never
+// frees its tensor memory or exits while its own asynchronous work is in flight
+// (that work completes in microseconds unless the GPU is wedged).
+__device__ __forceinline__ unsigned long long drain_ns(long long timeout_ns) {
+    return (unsigned long long)(timeout_ns > 1000000000LL ? timeout_ns : 1000000000LL);
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
                                             uint32_t bar) {
     asm volatile(
