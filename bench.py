@@ -139,22 +139,69 @@ def _recorded_traffic(kernel: str):
     return None
 
 
-def _cpu_baseline(pr, seconds_hint=True):
+def _cpu_baseline(pr, seconds_hint=True, single_thread=False, grads_to_b2=None):
     """The oracle, as it stands, on the host cores: the first 500 unadjusted
-    iterations of the same ensemble (all M chains)."""
+    iterations of the same ensemble (all M chains).  single_thread adds the same
+    on one core (first 50 iterations); grads_to_b2 (gradients per chain the GPU
+    run needed to reach b^2 < 0.01) adds the oracle's projected time to it."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
     tg = oracle.OracleTarget(pr.kind, pr.d, prec=pr.prec, banana_sb=pr.banana_sb,
                              funnel_sv=pr.funnel_sv)
-    run = oracle.OracleLAPS(tg, pr.x0, seed=0, n_total_steps=pr.n_steps)
+
+    def rate(n_it):
+        run = oracle.OracleLAPS(tg, pr.x0, seed=0, n_total_steps=pr.n_steps)
+        t0 = time.perf_counter()
+        run.iterate(n_it)
+        dt = time.perf_counter() - t0
+        return pr.M * (run.trace[-1]["grads"] - 1) / dt, dt
+
     n_it = 500
-    t0 = time.perf_counter()
-    run.iterate(n_it)
-    dt = time.perf_counter() - t0
-    grads = run.trace[-1]["grads"] - 1
-    return {"value": pr.M * grads / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "FP64 oracle, %d chains x first %d unadjusted iterations of %s (%.1f s)"
-                      % (pr.M, n_it, pr.name, dt)}
+    v, dt = rate(n_it)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "FP64 oracle, %d chains x first %d unadjusted iterations of %s (%.1f s)"
+                     % (pr.M, n_it, pr.name, dt)}
+    if grads_to_b2:
+        out["projected_time_to_b2_s"] = pr.M * grads_to_b2 / v
+    if single_thread:
+        oracle.set_threads(1)
+        v1, dt1 = rate(50)
+        oracle.set_threads(cores)
+        out["single_thread"] = {"value": v1, "cores": 1,
+                                "sample": "first 50 unadjusted iterations (%.1f s)" % dt1}
+        if grads_to_b2:
+            out["single_thread"]["projected_time_to_b2_s"] = pr.M * grads_to_b2 / v1
+    return out
+
+
+def _probe_peaks(stream):
+    """Throughput probes of this GPU (laps_measure_peaks), and cuBLAS TF32 and
+    FP64 GEMM throughput through torch (library GEMMs, for the tensor-core rates
+    of those types; 8192^3 TF32, 4096^3 FP64)."""
+    import torch
+    from paper_2601_16696_gb300 import laps
+    out = laps.measure_peaks(stream)
+
+    def gemm_tflops(n, dtype, reps):
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        torch.matmul(a, b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        out["tf32_gemm_tflops"] = gemm_tflops(8192, torch.float32, 10)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["fp64_gemm_tflops"] = gemm_tflops(4096, torch.float64, 3)
+    return out
 
 
 def run_reference(args):
@@ -628,8 +675,10 @@ def main():
         }
         if not args.no_forms:
             line["forms"] = _forms(flush, stream, mhz, seed_base + 500)
+            line["measured_peaks"] = _probe_peaks(stream)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = _cpu_baseline(pr)
+            line["cpu_baseline"] = _cpu_baseline(pr, single_thread=True,
+                                                 grads_to_b2=time_to_b2.get("grads_per_chain"))
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -298,6 +298,25 @@ typedef struct {
 } laps_launch_info;
 laps_status laps_get_launch_info(const laps_ctx* ctx, laps_launch_info* out);
 
+/* Throughput probes of the current GPU, the denominators of the kernels'
+ * roofline fractions at the clock the GPU actually runs at: FP32 and FP64
+ * fused multiply-add throughput over all SMs, the special-function unit's
+ * base-2 exponential per clock and SM, and the latency of the grid-wide
+ * barrier the persistent kernels use (one block per SM, cooperative launch).
+ * Each probe is timed with CUDA events on `stream` after one warm-up launch;
+ * the call synchronises the stream and takes a few milliseconds.  Returns
+ * LAPS_ERR_TIMEOUT if a barrier wait expired (2 s bound). */
+typedef struct {
+    int sm_count;
+    double sm_mhz;            /* SM clock during the FP32 probe (cycle counter / global timer) */
+    double fp32_tflops;       /* FFMA, 2 FLOP each */
+    double fp64_tflops;       /* DFMA, 2 FLOP each */
+    double ex2_per_clk_sm;    /* ex2.approx.f32 results per clock per SM */
+    double grid_barrier_us;   /* one grid barrier of barrier_blocks blocks */
+    int barrier_blocks;
+} laps_peaks;
+laps_status laps_measure_peaks(laps_peaks* out, void* stream);
+
 /* ---- many problems in one launch -----------------------------------------
  * A batch of independent diagonal-Gaussian problems of uneven dimension and
  * ensemble size (the paper runs one problem per call; batching is this

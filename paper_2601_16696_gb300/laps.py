@@ -103,6 +103,12 @@ class LaunchInfo(C.Structure):
                 ("resident", C.c_int)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int), ("sm_mhz", C.c_double), ("fp32_tflops", C.c_double),
+                ("fp64_tflops", C.c_double), ("ex2_per_clk_sm", C.c_double),
+                ("grid_barrier_us", C.c_double), ("barrier_blocks", C.c_int)]
+
+
 def _as_dict(s):
     return {n: getattr(s, n) for n, _ in s._fields_}
 
@@ -138,6 +144,7 @@ SIGNATURES = {
     "laps_normals": (C.c_int, [C.c_uint64, C.c_uint32, C.c_int64, C.c_uint32, C.c_uint32,
                                C.c_uint32, C.c_int64, _vp, _vp]),
     "laps_get_launch_info": (C.c_int, [_vp, C.POINTER(LaunchInfo)]),
+    "laps_measure_peaks": (C.c_int, [C.POINTER(Peaks), _vp]),
     "laps_run_noalloc": (C.c_int, [C.POINTER(TargetDesc), C.c_int64, C.POINTER(Config), _vp,
                                    C.c_double, C.c_uint64, _vp, C.POINTER(Stats), _vp]),
     "laps_batch_create": (C.c_int, [C.POINTER(Problem), C.c_int, C.POINTER(Config),
@@ -380,6 +387,14 @@ class Sampler:
         li = LaunchInfo()
         _check(lib().laps_get_launch_info(self._h, C.byref(li)))
         return _as_dict(li)
+
+
+def measure_peaks(stream=None) -> dict:
+    """Throughput probes of the current GPU (FP32 / FP64 FMA, ex2 per clock,
+    grid-barrier latency, SM clock); synchronises the stream."""
+    p = Peaks()
+    _check(lib().laps_measure_peaks(C.byref(p), _stream(stream)))
+    return _as_dict(p)
 
 
 def philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
