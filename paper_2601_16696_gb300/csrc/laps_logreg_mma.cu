@@ -5,8 +5,8 @@
 // A CTA owns 128 chains (one MMA M tile) and one range of data rows, which it
 // walks in chunks of 64 rows:
 //   Z_c  = [W_hi | W_lo] [X_c | X_c]^T     128 x 64, K = 2 kp   (TMEM, two buffers)
-//   R_c  = y_c - sigmoid(Z_c)  (BF16, swizzled into shared memory by the epilogue)
-//   G   += R_c X_c                          128 x kp, K = 64     (TMEM)
+//   R_c  = y_c - sigmoid(Z_c)  (BF16, written into tensor memory by the epilogue)
+//   G   += R_c X_c                          128 x kp, K = 64     (TMEM; R read from TMEM)
 // W = x is split into two BF16 terms (hi + lo carries ~16 significant bits),
 // so the logits are those of the BF16-rounded data at nearly FP32 accuracy in
 // x and log p stays smooth along a trajectory; R is a single BF16 term.
@@ -33,7 +33,7 @@ namespace {
 
 constexpr int MT = 128;      // chains per CTA (MMA M)
 constexpr int TNR = 64;      // data rows per chunk (MMA N of Z, K of G)
-constexpr int NSTAGE = 3;    // X / X^T ring depth
+constexpr int NSTAGE = 4;    // X / X^T ring depth
 constexpr int NTHR = 640;
 constexpr int EPI_WARP0 = 4;  // first epilogue warp
 constexpr int NEPI = 16;      // epilogue warps: 4 lane quarters x 4 column quarters
@@ -83,14 +83,15 @@ struct Smem {
     static constexpr uint32_t X_BYTES = (uint32_t)NA * TNR * 128;
     static constexpr uint32_t XT_BYTES = (uint32_t)KP * 128;
     static constexpr uint32_t STAGE = X_BYTES + XT_BYTES;
-    static constexpr uint32_t R_BYTES = MT * 128;
     static constexpr uint32_t OFF_W = 0;
     static constexpr uint32_t OFF_X = OFF_W + W_BYTES;
-    static constexpr uint32_t OFF_R = OFF_X + NSTAGE * STAGE;
-    static constexpr uint32_t OFF_BAR = OFF_R + 2 * R_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_X + NSTAGE * STAGE;
     static constexpr uint32_t OFF_LP = OFF_BAR + 256;      // [4][MT] float-float
     static constexpr uint32_t TOTAL = OFF_LP + 4 * MT * 8 + 1024;  // + alignment slack
-    static constexpr uint32_t TMEM_COLS = 2 * TNR + KP <= 256 ? 256 : 512;
+    // tensor memory: Z buffers [0, 128), G [128, 128 + kp), R buffers (64 BF16 rows
+    // per chain = 32 columns each) after G
+    static constexpr uint32_t T_R = 2 * TNR + KP, TMEM_COLS = T_R + 2 * (TNR / 2) <= 256 ? 256 : 512;
+    static_assert(T_R + TNR <= TMEM_COLS, "tensor memory columns");
 };
 
 enum { B_WFULL = 0, B_XFULL = 1, B_XEMPTY = B_XFULL + NSTAGE, B_ZFULL = B_XEMPTY + NSTAGE,
@@ -108,7 +109,7 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
     const uint32_t raw = smem_u32(mma_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned for the swizzle atoms
     unsigned char* gbase = mma_smem_raw + (base - raw);
-    const uint32_t sW = base + S::OFF_W, sX = base + S::OFF_X, sR = base + S::OFF_R;
+    const uint32_t sW = base + S::OFF_W, sX = base + S::OFF_X;
     const uint32_t bars = base + S::OFF_BAR;
     ff* s_lp = reinterpret_cast<ff*>(gbase + S::OFF_LP);
     auto bar = [&](int k) { return bars + 8u * (uint32_t)k; };
@@ -148,7 +149,7 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t tZ = tmem, tG = tmem + 2 * TNR;  // columns: Z buffers [0, 128), G [128, 128 + kp)
+    const uint32_t tZ = tmem, tG = tmem + 2 * TNR, tR = tmem + S::T_R;
 
     if (warp == 0) {
       if (lane == 0) {
@@ -189,11 +190,11 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
             const int rb = cc & 1, st = cc % NSTAGE;
             if (!mbar_wait(bar(B_RFULL + rb), (cc >> 1) & 1, deadline)) return false;
             tc_fence_after();
-            const uint32_t aR = sR + (uint32_t)rb * S::R_BYTES;
+            const uint32_t aR = tR + (uint32_t)rb * (TNR / 2);
             const uint32_t bXt = sX + (uint32_t)st * S::STAGE + S::X_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TNR / 16; ++kk)
-                tc_mma(tG, sw128_desc(aR + 32u * kk), sw128_desc(bXt + 32u * kk), ID_G,
+                tc_mma_ts(tG, aR + 8u * kk, sw128_desc(bXt + 32u * kk), ID_G,
                        (cc > 0 || kk > 0) ? 1u : 0u);
             tc_commit(bar(B_REMPTY + rb));
             tc_commit(bar(B_XEMPTY + st));
@@ -292,19 +293,13 @@ logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_con
             lp = ff_add(lp, lsum);
             const int rb = zb;
             if (!mbar_wait(bar(B_REMPTY + rb), ((c >> 1) & 1) ^ 1, deadline)) { ok = false; break; }
-            // R row rt, 16-byte chunks 2h, 2h+1 of the 128-byte row, 128-byte swizzle
-            unsigned char* rrow = gbase + S::OFF_R + (size_t)rb * S::R_BYTES + (size_t)rt * 128;
+            // R row rt, data rows 16h .. 16h+15: columns 8h .. 8h+7 of this lane's R buffer
+            uint32_t pr[8];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int chunk = (2 * h + t) ^ (rt & 7);
-                uint4 v;
-                v.x = pack_bf16(r[8 * t + 0], r[8 * t + 1]);
-                v.y = pack_bf16(r[8 * t + 2], r[8 * t + 3]);
-                v.z = pack_bf16(r[8 * t + 4], r[8 * t + 5]);
-                v.w = pack_bf16(r[8 * t + 6], r[8 * t + 7]);
-                *reinterpret_cast<uint4*>(rrow + 16 * chunk) = v;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int e = 0; e < 8; ++e) pr[e] = pack_bf16(r[2 * e], r[2 * e + 1]);
+            tmem_st8(tR + lane_off + (uint32_t)(rb * (TNR / 2) + 8 * h), pr);
+            tmem_st_wait();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_RFULL + rb));
         }
