@@ -27,6 +27,7 @@ import argparse
 import json
 import math
 import os
+import dataclasses
 import statistics
 import subprocess
 import sys
@@ -171,6 +172,43 @@ def _cpu_baseline(pr, seconds_hint=True, single_thread=False, grads_to_b2=None):
                                 "sample": "first 50 unadjusted iterations (%.1f s)" % dt1}
         if grads_to_b2:
             out["single_thread"]["projected_time_to_b2_s"] = pr.M * grads_to_b2 / v1
+    return out
+
+
+def _oracle_rates():
+    """The oracle, as it stands, on all host cores on a short slice of each of
+    the other workloads (chain-gradient-evals/s; the slices are stated): the
+    Gaussian (M = 256) and the funnel (M = 4096) for 50 and 20 unadjusted
+    iterations, the logistic regression (M = 8192, n = 10^4) for 2, the batch's
+    64 small problems for 1, and its d = 10^4 problem for 1 on 1024 of its chains."""
+    import oracle
+    from paper_2601_16696_gb300 import workloads
+    cores = oracle.set_threads(os.cpu_count() or 1)
+
+    def ot(pr):
+        if pr.kind == workloads.LOGREG:
+            return oracle.OracleTarget(pr.kind, pr.d, X=pr.X, y=pr.y, prior_var=pr.prior_var)
+        return oracle.OracleTarget(pr.kind, pr.d, prec=pr.prec, banana_sb=pr.banana_sb,
+                                   funnel_sv=pr.funnel_sv)
+
+    def rate(probs, n_it):
+        evals, dt = 0, 0.0
+        for k, pr in enumerate(probs):
+            run = oracle.OracleLAPS(ot(pr), pr.x0, seed=0, pid=k, n_total_steps=pr.n_steps)
+            t0 = time.perf_counter()
+            run.iterate(n_it)
+            dt += time.perf_counter() - t0
+            evals += pr.M * (run.trace[-1]["grads"] - 1)
+        return {"value": evals / dt, "unit": UNIT, "seconds": dt}
+
+    out = {"cores": cores, "kind": "oracle"}
+    out["gauss_d100_M256"] = rate([workloads.gauss_diag()], 50) | {"sample": "50 unadjusted iterations"}
+    out["funnel_d101_M4096"] = rate([workloads.funnel()], 20) | {"sample": "20 unadjusted iterations"}
+    out["logreg_d101_n10000_M8192"] = rate([workloads.logreg()], 2) | {"sample": "2 unadjusted iterations"}
+    probs = workloads.batch64()
+    out["batch64_small"] = rate(probs[:-1], 1) | {"sample": "1 unadjusted iteration of the 64 small problems"}
+    big = dataclasses.replace(probs[-1], M=1024, x0=probs[-1].x0[:1024])
+    out["batch64_big_d10000"] = rate([big], 1) | {"sample": "1 unadjusted iteration of its first 1024 chains"}
     return out
 
 
@@ -679,6 +717,8 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(pr, single_thread=True,
                                                  grads_to_b2=time_to_b2.get("grads_per_chain"))
+            if not args.no_forms:
+                line["cpu_baseline"]["other_workloads"] = _oracle_rates()
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
