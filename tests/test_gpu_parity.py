@@ -195,7 +195,7 @@ def test_final_b2_within_10_percent(L, ora, name, kw, cfg, key):
 
 
 def test_funnel_whole_run_statistics(L, ora):
-    """The funnel (configs[2] shape, 2000 steps, switch forced at step 400).
+    """The funnel (d = 101, M = 4096, 2000 steps, switch forced at step 400).
     Its b^2 is not a usable bar: Var[x_i^2] is astronomically large, so b^2
     is ~5e-5 and spreads by 20% (b^2_avg) to 5x (b^2_max) between oracle seeds.
     The GPU run is held to what four oracle seeds agree on: the phase machine
