@@ -30,7 +30,9 @@ template <int Q, int CW>
 __global__ void __launch_bounds__(kThreads) gauss_dense_grad_kernel(const float* __restrict__ P, int d,
                                                                      const float* __restrict__ W, int64_t M,
                                                                      float* __restrict__ G,
-                                                                     float2* __restrict__ LP) {
+                                                                     float2* __restrict__ LP,
+                                                                     const int* __restrict__ guard) {
+    if (guard != nullptr && *guard == 0) return;  // the iteration no longer runs
     constexpr int dp = 32 * Q, nch = 8 * CW;
     extern __shared__ __align__(16) float sm[];
     float* Xs = sm;                 // [nch][dp]
@@ -98,7 +100,8 @@ __global__ void __launch_bounds__(kThreads) gauss_dense_grad_kernel(const float*
 }
 
 template <int Q>
-cudaError_t launch_q(const float* P, int d, const float* W, int64_t M, float* G, float2* LP, cudaStream_t st) {
+cudaError_t launch_q(const float* P, int d, const float* W, int64_t M, float* G, float2* LP, cudaStream_t st,
+                     const int* guard) {
     // accumulators: 2 CW Q registers; 8 CW chains per block, so that the ensembles
     // of a few thousand chains give every SM a block or more
     constexpr int CW = Q <= 8 ? 2 : 1;
@@ -107,18 +110,18 @@ cudaError_t launch_q(const float* P, int d, const float* W, int64_t M, float* G,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (M + 8 * CW - 1) / (8 * CW);
-    gauss_dense_grad_kernel<Q, CW><<<(unsigned)blocks, kThreads, smem, st>>>(P, d, W, M, G, LP);
+    gauss_dense_grad_kernel<Q, CW><<<(unsigned)blocks, kThreads, smem, st>>>(P, d, W, M, G, LP, guard);
     return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t gauss_dense_grad(const float* P, int d_pad, int d, const float* W, int64_t M, float* G,
-                             float2* LP, cudaStream_t st) {
+                             float2* LP, cudaStream_t st, const int* guard) {
     if (M <= 0) return cudaSuccess;
     if (d_pad % 32 || d_pad < 32 || d_pad > kDenseMaxDim || M > (1LL << 30)) return cudaErrorInvalidValue;
     switch (d_pad / 32) {
 #define LAPS_Q(n) \
-    case n: return launch_q<n>(P, d, W, M, G, LP, st);
+    case n: return launch_q<n>(P, d, W, M, G, LP, st, guard);
         LAPS_Q(1) LAPS_Q(2) LAPS_Q(3) LAPS_Q(4) LAPS_Q(5) LAPS_Q(6) LAPS_Q(7) LAPS_Q(8)
         LAPS_Q(9) LAPS_Q(10) LAPS_Q(11) LAPS_Q(12) LAPS_Q(13) LAPS_Q(14) LAPS_Q(15) LAPS_Q(16)
 #undef LAPS_Q

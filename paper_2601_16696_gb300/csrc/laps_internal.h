@@ -100,8 +100,9 @@ constexpr int kDenseMaxDim = 512;
 // forms of the logistic-regression contraction: FP32 on the CUDA cores, BF16
 // tensor cores, tensor cores at FP32 accuracy (three-term BF16 split)
 enum GradForm : int { GF_F32 = 0, GF_BF16 = 1, GF_X3 = 2 };
+// (guard: as for the logistic-regression gradients, laps_logreg.cuh)
 cudaError_t gauss_dense_grad(const float* P, int d_pad, int d, const float* W, int64_t M, float* G,
-                             float2* LP, cudaStream_t st);
+                             float2* LP, cudaStream_t st, const int* guard = nullptr);
 inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_GAUSS_DENSE || kind == TGT_USER; }
 // USER targets: calls the callback for W [M][ld] and converts its FP32 log p into
 // the float-float partial the chain updates read (lp32: device [M] scratch)

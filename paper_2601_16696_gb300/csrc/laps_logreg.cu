@@ -29,7 +29,8 @@ template <int KP>
 __global__ void __launch_bounds__(NT, KP <= 128 ? 2 : 1)
 logreg_grad_f32_kernel(const float* __restrict__ W, int64_t M, const float* __restrict__ X,
                        const float* __restrict__ yv, int n, int rps, float inv_v,
-                       float* __restrict__ gpart, float2* __restrict__ lpart) {
+                       float* __restrict__ gpart, float2* __restrict__ lpart, const int* __restrict__ guard) {
+    if (guard != nullptr && *guard == 0) return;  // the iteration no longer runs
     constexpr int LD = KP + 4;   // padded row stride (floats) of the W and X tiles
     constexpr int NG = KP / 64;  // float4 column groups per thread in the G phase
     extern __shared__ __align__(16) float sm[];
@@ -178,28 +179,28 @@ size_t f32_smem() {
 
 template <int KP>
 cudaError_t launch_f32(const LogregData& D, const float* W, int64_t M, int S, float* gpart,
-                       float2* lpart, cudaStream_t st) {
+                       float2* lpart, cudaStream_t st, const int* guard) {
     const size_t smem = f32_smem<KP>();
     cudaError_t e = cudaFuncSetAttribute(logreg_grad_f32_kernel<KP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int rps = (D.n + S - 1) / S;
     const dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)S);
-    logreg_grad_f32_kernel<KP><<<grid, NT, smem, st>>>(W, M, D.X, D.y, D.n, rps, D.inv_v, gpart, lpart);
+    logreg_grad_f32_kernel<KP><<<grid, NT, smem, st>>>(W, M, D.X, D.y, D.n, rps, D.inv_v, gpart, lpart, guard);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t logreg_grad_f32(const LogregData& D, const float* W, int64_t M, int S, float* gpart,
-                            float2* lpart, cudaStream_t st) {
+                            float2* lpart, cudaStream_t st, const int* guard) {
     if (M <= 0) return cudaSuccess;
     if (S < 1 || S > 65535 || (M + TM - 1) / TM > 0x7fffffff) return cudaErrorInvalidValue;
     switch (D.kp) {
-    case 64: return launch_f32<64>(D, W, M, S, gpart, lpart, st);
-    case 128: return launch_f32<128>(D, W, M, S, gpart, lpart, st);
-    case 192: return launch_f32<192>(D, W, M, S, gpart, lpart, st);
-    case 256: return launch_f32<256>(D, W, M, S, gpart, lpart, st);
+    case 64: return launch_f32<64>(D, W, M, S, gpart, lpart, st, guard);
+    case 128: return launch_f32<128>(D, W, M, S, gpart, lpart, st, guard);
+    case 192: return launch_f32<192>(D, W, M, S, gpart, lpart, st, guard);
+    case 256: return launch_f32<256>(D, W, M, S, gpart, lpart, st, guard);
     }
     return cudaErrorInvalidValue;
 }

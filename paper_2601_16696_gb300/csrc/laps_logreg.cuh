@@ -49,7 +49,7 @@ cudaError_t logreg_pack_points(const float* x, int64_t M, int d, int kp, float* 
 // points (prior terms); a bounded wait that expires sets *status
 cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W32, int64_t M, int S,
                             int rps, float* gpart, float2* lpart, int* status, long long timeout_ns,
-                            cudaStream_t st);
+                            cudaStream_t st, const int* guard = nullptr);
 
 // ---- tensor-core gradient at FP32 accuracy (three-term BF16 split): laps_logreg_x3.cu
 bool logreg_x3_supported(int kp);
@@ -61,13 +61,17 @@ int logreg_x3_splits(const LogregData& D, int64_t M, int nsm, int* rps);
 // gradient partials like logreg_grad_f32 from the FP32 points W32 [M][kp], the
 // data split by logreg_x3_splits; a bounded wait that expires sets *status
 cudaError_t logreg_grad_x3(const LogregData& D, const float* W32, int64_t M, int S, int rps, float* gpart,
-                           float2* lpart, int* status, long long timeout_ns, cudaStream_t st);
+                           float2* lpart, int* status, long long timeout_ns, cudaStream_t st,
+                           const int* guard = nullptr);
 
 // log p and gradient at the M points W [M][kp] (x-space, padding columns 0),
 // with the data split into S row ranges: gpart [S][M][kp] and lpart [S][M]
 // (float-float) receive the per-range sums; range 0 also carries the prior.
-// The consumer adds the S partials in order.
+// The consumer adds the S partials in order.  Every gradient entry point takes
+// an optional guard: a device word that a launch earlier on the stream set to 0
+// when this evaluation belongs to an iteration that no longer runs (past a stop
+// or a switch); the kernel then returns at once.
 cudaError_t logreg_grad_f32(const LogregData& D, const float* W, int64_t M, int S, float* gpart,
-                            float2* lpart, cudaStream_t st);
+                            float2* lpart, cudaStream_t st, const int* guard = nullptr);
 
 }  // namespace laps

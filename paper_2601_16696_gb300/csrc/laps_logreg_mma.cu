@@ -74,6 +74,7 @@ struct MmaArgs {
     float2* lpart;       // [S][M]
     int* status;
     long long timeout_ns;
+    const int* guard;    // nullable: 0 there means the iteration no longer runs
 };
 
 template <int KP>
@@ -102,6 +103,7 @@ template <int KP>
 __global__ void __launch_bounds__(NTHR, 1)
 logreg_grad_mma_kernel(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmX,
                        const __grid_constant__ CUtensorMap tmXt, const MmaArgs A) {
+    if (A.guard != nullptr && *A.guard == 0) return;  // uniform: before any barrier or allocation
     using S = Smem<KP>;
     extern __shared__ __align__(1024) unsigned char mma_smem_raw[];
     __shared__ uint32_t s_tmem;
@@ -471,7 +473,7 @@ int logreg_mma_splits(const LogregData& D, int64_t M, int nsm, int* rps_out) {
 
 cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W32, int64_t M, int S,
                             int rps, float* gpart, float2* lpart, int* status, long long timeout_ns,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int* guard) {
     if (M <= 0) return cudaSuccess;
     MmaArgs a;
     a.M = M;
@@ -484,6 +486,7 @@ cudaError_t logreg_grad_mma(const LogregData& D, const void* tmW, const float* W
     a.lpart = lpart;
     a.status = status;
     a.timeout_ns = timeout_ns;
+    a.guard = guard;
     const dim3 grid((unsigned)((M + MT - 1) / MT), (unsigned)S);
     const CUtensorMap& mw = *reinterpret_cast<const CUtensorMap*>(tmW);
     const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(D.tmX);

@@ -74,6 +74,7 @@ struct X3Args {
     float2* lpart;       // [S][M]
     int* status;
     long long timeout_ns;
+    const int* guard;    // nullable: 0 there means the iteration no longer runs
 };
 
 template <int KP>
@@ -146,6 +147,7 @@ __device__ __forceinline__ float lg2_approx(float x) {
 template <int KP>
 __global__ void __launch_bounds__(NTHR, 1)
 logreg_grad_x3_kernel(const __grid_constant__ CUtensorMap tmX3, const X3Args A) {
+    if (A.guard != nullptr && *A.guard == 0) return;  // uniform: before any barrier or allocation
     using S = SmemX3<KP>;
     using B = Bars<KP>;
     constexpr int NST = S::NST, NRB = S::NRB;
@@ -520,7 +522,7 @@ cudaError_t logreg_x3_prepare(LogregData& D) {
 }
 
 cudaError_t logreg_grad_x3(const LogregData& D, const float* W32, int64_t M, int S, int rps, float* gpart,
-                           float2* lpart, int* status, long long timeout_ns, cudaStream_t st) {
+                           float2* lpart, int* status, long long timeout_ns, cudaStream_t st, const int* guard) {
     if (M <= 0) return cudaSuccess;
     if (D.X3b == nullptr) return cudaErrorInvalidValue;
     X3Args a;
@@ -535,6 +537,7 @@ cudaError_t logreg_grad_x3(const LogregData& D, const float* W32, int64_t M, int
     a.lpart = lpart;
     a.status = status;
     a.timeout_ns = timeout_ns;
+    a.guard = guard;
     if (D.kp == 64) return launch_x3<64>(D, a, S, st);
     if (D.kp == 128) return launch_x3<128>(D, a, S, st);
     return cudaErrorInvalidValue;

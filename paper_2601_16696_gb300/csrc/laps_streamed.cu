@@ -402,22 +402,25 @@ laps_status launch_seg(laps_ctx* c, const KParams& P, const SegOp& op, cudaStrea
 }
 
 // the gradient of the working points in contraction form `form` (GF_*; the
-// dense Gaussian and user targets have one form)
-laps_status launch_grad(laps_ctx* c, int form, cudaStream_t st) {
+// dense Gaussian and user targets have one form).  guard: the iteration's guard
+// word (the kernels return at once when it is 0: an iteration enqueued past a
+// stop or a switch), or null outside the iteration protocol.  A user callback
+// runs on the host's schedule and cannot read it.
+laps_status launch_grad(laps_ctx* c, int form, cudaStream_t st, const int* guard) {
     cudaError_t e;
     if (c->tg->kind == TGT_GAUSS_DENSE) {
-        e = gauss_dense_grad(c->tg->prec_dense, c->d_pad, c->d, c->W, c->M, c->gpart, c->lpart, st);
+        e = gauss_dense_grad(c->tg->prec_dense, c->d_pad, c->d, c->W, c->M, c->gpart, c->lpart, st, guard);
         return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
     }
     if (c->tg->kind == TGT_USER) return user_grad(c->tg, c->W, c->M, c->d_pad, c->gpart, c->ulp, c->lpart, st);
     if (form == GF_BF16)
         e = logreg_grad_mma(c->tg->lr, c->tmW, c->W, c->M, c->nsplit_mma, c->rps_mma, c->gpart, c->lpart,
-                            c->status, c->cfg.barrier_timeout_ns, st);
+                            c->status, c->cfg.barrier_timeout_ns, st, guard);
     else if (form == GF_X3)
         e = logreg_grad_x3(c->tg->lr, c->W, c->M, c->nsplit_x3, c->rps_x3, c->gpart, c->lpart, c->status,
-                           c->cfg.barrier_timeout_ns, st);
+                           c->cfg.barrier_timeout_ns, st, guard);
     else
-        e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st);
+        e = logreg_grad_f32(c->tg->lr, c->W, c->M, c->nsplit, c->gpart, c->lpart, st, guard);
     return e == cudaSuccess ? LAPS_OK
                             : cuda_fail(e, form == GF_BF16 ? "logreg gradient (tensor cores)"
                                            : form == GF_X3 ? "logreg gradient (tensor cores, three-term split)"
@@ -463,7 +466,7 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
         a.bB = c->cf.b[INTEG_LF][0];
         a.a = c->cf.a[INTEG_LF][0];
         LCK(launch_seg(c, P, a, st));
-        LCK(launch_grad(c, c->gf_unadj, st));
+        LCK(launch_grad(c, c->gf_unadj, st, c->go));
         SegOp b = seg_op(0);
         b.after_grad = 1;
         b.bA = c->cf.b[INTEG_LF][1];
@@ -483,14 +486,14 @@ laps_status enqueue_iteration(laps_ctx* c, int phase, cudaStream_t st) {
     LCK(launch_seg(c, P, a, st));
     for (int n = 0; n < N; ++n) {
         for (int s = 1; s < K - 1; ++s) {
-            LCK(launch_grad(c, c->gf_adj, st));
+            LCK(launch_grad(c, c->gf_adj, st, c->go));
             SegOp m = seg_op(1);
             m.after_grad = 1;
             m.bA = c->cf.b[I][s];
             m.a = c->cf.a[I][s];
             LCK(launch_seg(c, P, m, st));
         }
-        LCK(launch_grad(c, c->gf_adj, st));
+        LCK(launch_grad(c, c->gf_adj, st, c->go));
         SegOp e = seg_op(1);
         e.after_grad = 1;
         e.bA = c->cf.b[I][K - 1];
@@ -598,7 +601,7 @@ laps_status reevaluate_adjusted(laps_ctx* c, cudaStream_t st) {
     SegOp a = seg_op(1);
     a.init = 3;
     LCK(launch_seg(c, P, a, st));
-    LCK(launch_grad(c, c->gf_adj, st));
+    LCK(launch_grad(c, c->gf_adj, st, nullptr));
     SegOp b = seg_op(1);
     b.init = 4;
     LCK(launch_seg(c, P, b, st));
@@ -630,7 +633,7 @@ laps_status streamed_init(laps_ctx* c, const float* x0, float x0_scale, cudaStre
     a.first = 1;
     a.init = 1;
     LCK(launch_seg(c, P, a, st));
-    LCK(launch_grad(c, c->gf_unadj, st));
+    LCK(launch_grad(c, c->gf_unadj, st, nullptr));
     SegOp b = seg_op(0);
     b.init = 2;
     LCK(launch_seg(c, P, b, st));
