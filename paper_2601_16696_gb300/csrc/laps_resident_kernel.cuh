@@ -449,6 +449,38 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         LAPS_PHASE_MARK(1);
         // ------------------------------------------------ 2. block columns
         const int nq = ens_nq(P, H);
+        if (nq == NQ && P.qpp >= NQ) {
+            // all four quantities in one pass (the usual case): y, y^2, g, y g of each
+            // coordinate formed together; the same values and summation order as below
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int j = gl + LPC * k;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int q = 4 * k + c;
+                    const float yv = active ? y[q] : 0.0f, gv = active ? g[q] : 0.0f;
+                    const float v0 = across_groups<LPC>(yv), v1 = across_groups<LPC>(yv * yv);
+                    const float v2 = across_groups<LPC>(gv), v3 = across_groups<LPC>(yv * gv);
+                    if (grp == 0 && j < P.nblk) {
+                        float* row = sq + (size_t)warp * dp + 4 * j + c;
+                        row[0] = v0;
+                        row[(size_t)nwarps * dp] = v1;
+                        row[(size_t)2 * nwarps * dp] = v2;
+                        row[(size_t)3 * nwarps * dp] = v3;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int col = tid; col < NQ * dp; col += blockDim.x) {
+                const int qd = col / dp, i = col - qd * dp;
+                if (i >= P.d) continue;
+                ff s = ff_make(0.0f);
+                const float* src = sq + (size_t)qd * nwarps * dp + i;
+                for (int w = 0; w < nwarps; ++w) s = ff_add(s, src[(size_t)w * dp]);
+                P.part[((size_t)qd * dp + i) * G + blockIdx.x] = make_float2(s.hi, s.lo);
+            }
+            __syncthreads();
+        } else
         for (int q0 = 0; q0 < nq; q0 += P.qpp) {
             const int q1 = min(nq, q0 + P.qpp);
             for (int qd = q0; qd < q1; ++qd) {
