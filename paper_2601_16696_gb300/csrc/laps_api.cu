@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "laps_internal.h"
@@ -17,6 +19,17 @@ const void* resident_kernel_2(int lpc, int cpl, bool fr);
 const void* resident_kernel_4(int lpc, int cpl, bool fr);
 
 static thread_local std::string g_err;
+
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> granted;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& g = granted[fn];
+    if (bytes <= g) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g = bytes;
+    return e;
+}
 
 laps_status fail(laps_status st, const std::string& msg) {
     g_err = msg;
@@ -147,7 +160,7 @@ laps_status choose_shape(laps_ctx* c) {
             const size_t smem =
                 resident_smem(c->d_pad, threads, lpc, resident_smax(c->d, G), c->cfg.dtilde_K, kind);
             if (smem > 200 * 1024) continue;
-            CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CK(ensure_dyn_smem(fn, smem));
             int bps = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem));
             if ((long long)bps * nsm < G) continue;

@@ -654,7 +654,7 @@ cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, co
     const void* fn = batch_fn(cpl);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = batch_smem(cpl, cap_pad, SL);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dyn_smem(fn, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -681,7 +681,7 @@ cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, co
 int batch_blocks_per_sm(int cpl, int cap_pad, int SL) {
     const void* fn = batch_fn(cpl);
     const size_t smem = batch_smem(cpl, cap_pad, SL);
-    if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (!fn || ensure_dyn_smem(fn, smem) != cudaSuccess)
         return 0;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBT, smem) != cudaSuccess) return 0;

@@ -74,6 +74,10 @@ struct laps_ctx {
 namespace laps {
 laps_status fail(laps_status st, const std::string& msg);
 laps_status cuda_fail(cudaError_t e, const char* what);
+// Let kernel fn use at least `bytes` of dynamic shared memory.  The limit is a
+// process-wide attribute of the function, so it is only ever raised: a context
+// that needs less must not lower it under another live context's launches.
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
 // shared by the context API and the allocation-free entry point (laps_api.cu)
 laps_status choose_shape(laps_ctx* c);
 laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st);

@@ -535,8 +535,7 @@ laps_status streamed_setup(laps_ctx* c) {
     c->seg_G = (int)((c->M + kSegWarps - 1) / kSegWarps);
     c->G = c->seg_G;
     c->seg_smem = (size_t)NQ * kSegWarps * dp * sizeof(float) + (size_t)kSegWarps * NCS * sizeof(ff);
-    e = cudaFuncSetAttribute(seg_fn(c->seg_cpl), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)c->seg_smem);
+    e = ensure_dyn_smem((const void*)seg_fn(c->seg_cpl), c->seg_smem);
     if (e != cudaSuccess) return cuda_fail(e, "seg_kernel attribute");
     c->fin_G = std::max(1, std::min(2 * nsm, c->d));
     c->smax = (c->d + c->fin_G - 1) / c->fin_G;
