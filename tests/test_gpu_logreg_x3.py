@@ -208,3 +208,17 @@ def test_x3_determinism_and_checkpoint(L):
     b.restore(blob)
     b.step(40)
     np.testing.assert_array_equal(a.sample().cpu().numpy(), b.sample().cpu().numpy())
+
+
+def test_precision_values_checked(L):
+    pr = W.logreg(n_data=200, n_feat=20, M=64, n_steps=10)
+    tg = L.Target.from_problem(pr)
+    with pytest.raises(L.LapsError) as e:
+        L.Sampler(tg, pr.M, n_total_steps=10, precision=7)
+    assert e.value.status == 1  # LAPS_ERR_INVALID_ARG
+    g = W.gauss_diag(d=10, M=64, n_steps=10)
+    gt = L.Target.from_problem(g)
+    for p in (BF16X3, MIXED_BF16X3):
+        with pytest.raises(L.LapsError) as e:
+            L.Sampler(gt, g.M, n_total_steps=10, precision=p)
+        assert e.value.status == 6  # LAPS_ERR_UNSUPPORTED: the split forms are LOGREG's
