@@ -258,8 +258,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "%s_M%d (oracle sample: first 500 unadjusted iterations)"
-                       % (pr.name, pr.M)},
+            "config": {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
+                       "switch": "after %d unadjusted steps (first full window)" % WORKLOAD["switch_at"],
+                       "parallelism": "host cores (the oracle)"},
             "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v,
                                                                                     "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
