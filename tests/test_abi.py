@@ -44,12 +44,14 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2601_16696_gb300 import laps
     prog = tmp_path / "sizes.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "laps.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d %d %d %d\\n",'
                     'sizeof(laps_config), sizeof(laps_stats), sizeof(laps_trace_row),'
                     'sizeof(laps_target_desc), sizeof(laps_launch_info),'
                     'offsetof(laps_config, barrier_extra_arrivals),'
                     'offsetof(laps_stats, b2_first_ns), sizeof(laps_problem),'
-                    'offsetof(laps_problem, x0_scale), sizeof(laps_batch_shape));return 0;}\n')
+                    'offsetof(laps_problem, x0_scale), sizeof(laps_batch_shape),'
+                    'sizeof(laps_peaks), offsetof(laps_peaks, grid_barrier_us),'
+                    '(int)LAPS_FP32, (int)LAPS_MIXED, (int)LAPS_BF16X3, (int)LAPS_MIXED_BF16X3);return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HDR), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
@@ -58,7 +60,9 @@ def test_struct_layouts_match_c(tmp_path):
     want = [C.sizeof(laps.Config), C.sizeof(laps.Stats), C.sizeof(laps.TraceRow),
             C.sizeof(laps.TargetDesc), C.sizeof(laps.LaunchInfo),
             laps.Config.barrier_extra_arrivals.offset, laps.Stats.b2_first_ns.offset,
-            C.sizeof(laps.Problem), laps.Problem.x0_scale.offset, C.sizeof(laps.BatchShape)]
+            C.sizeof(laps.Problem), laps.Problem.x0_scale.offset, C.sizeof(laps.BatchShape),
+            C.sizeof(laps.Peaks), laps.Peaks.grid_barrier_us.offset,
+            laps.FP32, laps.MIXED, laps.BF16X3, laps.MIXED_BF16X3]
     assert got == want
 
 
