@@ -6,10 +6,10 @@ diagnostic build, not the product library).
 builds the library with -DLAPS_PHASE_TIMING (and LAPS_PHASE_BLOCK = block,
 default 0) into liblaps_phase<block>.so beside the product library, runs the
 banana workload (d = 100, M = 4096) for 500 unadjusted iterations at a fixed
-step and for 40 MAMS proposals after a switch at step 1000, and prints the
-mean microseconds per iteration between the kernel's phase marks (the marks
-synchronise the block, so the sum is a little above the undisturbed
-iteration).
+step, 500 with the step-size controller, and 40 MAMS proposals after a switch
+at step 1000, and prints the mean microseconds per iteration between the
+kernel's phase marks (the marks synchronise the block, so the sum is not
+exactly the undisturbed iteration).
 """
 import ctypes as C
 import os
@@ -34,6 +34,7 @@ def main(block: int = 0) -> None:
     tg = laps.Target.from_problem(pr)
     x0 = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
     for label, cfg, warm, n in (("unadjusted, fixed step", dict(fixed_eps=0.05), 20, 500),
+                                ("unadjusted, adaptive step", dict(adjusted=0), 20, 500),
                                 ("adjusted, switch at step 1000", dict(force_switch_at=1000), 1010, 40)):
         s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, **cfg)
         L.laps_debug_phase_ns(s._h, None)
