@@ -21,8 +21,25 @@
  *    coordinate i of chain m, FP32.  A device pointer that is not 4-byte
  *    aligned returns LAPS_ERR_INVALID_ARG.
  *  - All GPU work is ordered on the cudaStream_t argument (pass it as a
- *    void*; NULL is the legacy default stream).  Only laps_get_stats,
- *    laps_get_trace, laps_checkpoint and laps_restore synchronise.
+ *    void*; NULL is the legacy default stream).  These calls block the host:
+ *     - set-up calls that allocate or copy host arrays in: laps_target_create,
+ *       laps_create, laps_set_truth, laps_batch_create, laps_batch_set_truth,
+ *       laps_batch_set_shape (device-synchronous);
+ *     - calls that read results back: laps_get_stats, laps_get_trace,
+ *       laps_checkpoint, laps_restore, laps_adapt_freeze, laps_target_status,
+ *       laps_batch_get_stats, laps_batch_get_trace, laps_batch_tune,
+ *       laps_measure_peaks, and laps_run_noalloc when stats_out is not NULL;
+ *     - laps_step and laps_run of a context on the streamed path (a LOGREG or
+ *       USER target, a GAUSS_DENSE target beyond d = 128 or with
+ *       dense_streamed): the host enqueues a different launch sequence for an
+ *       unadjusted step and for a MAMS proposal, so it reads the phase machine
+ *       back (a stream synchronisation) every 32 unadjusted iterations or 4
+ *       proposals, and at the switch.
+ *    Every other call (laps_init, laps_step and laps_run of the
+ *    register-resident path, laps_sample, laps_get_state, laps_philox,
+ *    laps_normals, laps_target_logp_grad[_prec], laps_batch_init,
+ *    laps_batch_step, laps_batch_run, laps_batch_sample) only enqueues work
+ *    and returns.
  *  - Errors raised inside a kernel (a bounded wait that expired, a bad
  *    parameter) are latched in a device status word and returned by the next
  *    call that reads it (laps_get_stats, or any synchronising call).
@@ -276,17 +293,28 @@ laps_status laps_normals(uint64_t seed, uint32_t m0, int64_t nm, uint32_t t, uin
  * not grow the device footprint after loading).
  * One complete run (laps_init with x0 / x0_scale / seed, then laps_run) of a
  * GAUSS_DIAG, BANANA or FUNNEL target described by desc (its device arrays
- * are read, not copied into any allocation); the samples go to x_out device
- * [M][d]; if stats_out is not NULL the call synchronises the stream and fills
- * it.  No trace is kept and laps_set_truth does not apply (b^2 fields NaN).
- * All scratch lives in one fixed 16 MiB __device__ array of the library that
- * every GPU loading the library holds until exit; a problem needing more
- * (about 12 M d bytes of state plus the window and reduction buffers) returns
- * LAPS_ERR_INVALID_ARG before any launch.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress): make that first call
- * before any stream capture.  Every call on a device shares the array and
- * clears what must start at zero; calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised. */
+ * are read, not copied into any allocation), in FP32 (cfg->precision must be
+ * LAPS_FP32, cfg->stop_b2 0 and cfg->dtilde_K 0, else LAPS_ERR_UNSUPPORTED);
+ * the samples go to x_out device [M][d].  With stats_out NULL the call only
+ * enqueues work on the stream; otherwise it synchronises the stream and fills
+ * stats_out.  No trace is kept and laps_set_truth does not apply (b^2 fields
+ * NaN).
+ * All scratch lives in one fixed 16 MiB __device__ array of the library, held
+ * on a device until the process exits once the library's device code is
+ * loaded there.  Under CUDA's lazy module loading (the default) that happens
+ * at the first call on the device, so that call may still grow the device
+ * footprint: a caller that hands the rest of the device to a pool should make
+ * it first, or make the set-up-only call laps_run_noalloc(NULL, 0, NULL, NULL,
+ * 0, 0, NULL, NULL, NULL), which loads the array and looks up its address and
+ * does nothing else (CUDA_MODULE_LOADING=EAGER loads it when the library is
+ * loaded instead).  A problem needing more (about 12 M d bytes of state plus
+ * the window and reduction buffers) returns LAPS_ERR_INVALID_ARG before any
+ * launch.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any
+ * stream capture, and do not cudaDeviceReset a device this entry point has
+ * run on (the cached address would be stale).  Every call on a device shares
+ * the array and clears what must start at zero; calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised. */
 laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M, const laps_config* cfg,
                              const float* x0, double x0_scale, uint64_t seed, float* x_out,
                              laps_stats* stats_out, void* stream);
@@ -357,7 +385,10 @@ laps_status laps_batch_init(laps_batch* b, uint64_t seed, void* stream);
  * finished idles).  Capturable in a CUDA graph. */
 laps_status laps_batch_step(laps_batch* b, int n_iters, void* stream);
 /* Runs every problem to its end: a CUDA graph of one launch of
- * iters_per_launch iterations, replayed until all problems are done. */
+ * iters_per_launch iterations, replayed n_total_steps / iters_per_launch + 2
+ * times (enough for a run that never switches); a launch that finds every
+ * problem done returns at once.  Enqueues only: read the outcome with
+ * laps_batch_get_stats. */
 laps_status laps_batch_run(laps_batch* b, int iters_per_launch, void* stream);
 /* Autotuner: times every feasible shape for two iterations from the current
  * state (restored afterwards) and keeps the fastest; synchronises. */

@@ -80,11 +80,25 @@ __global__ void fill_kernel(float* p, float v, int64_t n) {
          k += (int64_t)gridDim.x * blockDim.x)
         p[k] = v;
 }
+// the start of a run: the phase machine (taken by value, so no host memory is
+// referenced once the launch is enqueued), the status word and sigma = 1
+__global__ void run_start_kernel(Hyper* hyper, const Hyper h, int* status, float* sigma, int64_t d_pad) {
+    const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k0 == 0) {
+        *hyper = h;
+        *status = 0;
+    }
+    for (int64_t k = k0; k < d_pad; k += (int64_t)gridDim.x * blockDim.x) sigma[k] = 1.0f;
+}
+__global__ void set_coefs_kernel(Coefs* dst, const Coefs cf) { *dst = cf; }
 
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
 void launch_fill(float* p, float v, int64_t n, cudaStream_t st) {
     fill_kernel<<<grid_for(n), 256, 0, st>>>(p, v, n);
+}
+void launch_set_coefs(Coefs* dst, const Coefs& cf, cudaStream_t st) {
+    set_coefs_kernel<<<1, 1, 0, st>>>(dst, cf);
 }
 void launch_unpack(const float* src, const float* scale, float* dst, int64_t M, int d, int d_pad,
                    cudaStream_t st) {
@@ -549,16 +563,12 @@ Hyper initial_hyper() {
 // clears the run state (phase machine, status, window, preconditioner) and
 // launches the initialisation; no allocation
 laps_status start_run(laps_ctx* c, const float* x0, float x0_scale, cudaStream_t st) {
-    const Hyper h = initial_hyper();
-    CK(cudaMemcpyAsync(c->hyper, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->ring, 0, (size_t)(c->T + 1) * c->d_pad * 8, st));
     CK(cudaMemsetAsync(c->win_sums, 0, (size_t)c->d_pad * 16, st));
     CK(cudaMemsetAsync(c->cstat, 0, (size_t)c->d_pad * NCO * 4, st));
-    fill_kernel<<<grid_for(c->d_pad), 256, 0, st>>>(c->sigma, 1.0f, c->d_pad);
+    run_start_kernel<<<grid_for(c->d_pad), 256, 0, st>>>(c->hyper, initial_hyper(), c->status, c->sigma,
+                                                         c->d_pad);
     CK(cudaGetLastError());
-    // keep the caller's stream synchronous with the host copy of h above
-    CK(cudaStreamSynchronize(st));
     c->initialized = true;
     if (c->streamed) return streamed_init(c, x0, x0_scale, st);
     return launch_resident(c, 0, 1, x0, x0_scale, st);

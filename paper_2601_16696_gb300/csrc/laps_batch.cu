@@ -356,6 +356,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
         if (tid == 0) {
             int live = 0;
             for (int p = 0; p < B.n; ++p) live |= (B.mode == 0 || !B.probs[p].hyper->done) ? 1 : 0;
+            // a latched error ends the launch (a replayed graph launch after a failure is empty)
+            if (*reinterpret_cast<volatile int*>(B.status) != ST_OK) live = 0;
             s_live = live;
         }
         __syncthreads();

@@ -164,6 +164,44 @@ laps_status launch(laps_batch* b, int mode, int n_iters, cudaStream_t st) {
     return LAPS_OK;
 }
 
+// the start of a run of every problem: its seed in the parameter block, its
+// phase machine (h0, by value), a cleared window, column results and status,
+// sigma = 1; block k takes problems k, k + gridDim.x, ...
+__global__ void batch_start_kernel(KParams* probs, Hyper* hyper, int n, uint32_t seed_lo, uint32_t seed_hi,
+                                   const Hyper h0, int* status) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        KParams& P = probs[k];
+        if (threadIdx.x == 0) {
+            P.seed_lo = seed_lo;
+            P.seed_hi = seed_hi;
+            hyper[k] = h0;
+        }
+        const int dp = P.d_pad;
+        const size_t nring = (size_t)(P.T + 1) * dp;
+        for (size_t i = threadIdx.x; i < nring; i += blockDim.x) P.ring[i] = make_float2(0.0f, 0.0f);
+        for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+            P.win_sums[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            P.sigma[i] = 1.0f;
+        }
+        for (int i = threadIdx.x; i < dp * NCO; i += blockDim.x) P.cstat[i] = 0.0f;
+    }
+}
+
+// problem k's positions x = sigma o y, except after a switch that no proposal
+// followed (y is still in x then); the phase machine is read on the device
+__global__ void batch_unpack_kernel(const float* __restrict__ y, const float* __restrict__ sigma,
+                                    const Hyper* __restrict__ h, float* __restrict__ x, int64_t M, int d,
+                                    int d_pad) {
+    const bool pend = h->phase == 1 && h->p == 0;
+    const int64_t n = M * (int64_t)d;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = k / d;
+        const int i = (int)(k - m * d);
+        x[k] = (pend ? 1.0f : sigma[i]) * y[m * d_pad + i];
+    }
+}
+
 laps_status read_hypers(laps_batch* b) {
     BCK(cudaStreamSynchronize(b->last_stream));
     BCK(cudaMemcpy(b->h_hyper, b->hyper, sizeof(Hyper) * b->n, cudaMemcpyDeviceToHost));
@@ -331,19 +369,11 @@ laps_status laps_batch_set_truth(laps_batch* b, int k, const double* Ex2, const 
 laps_status laps_batch_init(laps_batch* b, uint64_t seed, void* stream) {
     if (!b) return fail(LAPS_ERR_INVALID_ARG, "null batch");
     cudaStream_t st = (cudaStream_t)stream;
-    b->seed = seed;
-    laps_status s = upload(b);
-    if (s != LAPS_OK) return s;
-    std::vector<Hyper> h(b->n, initial_hyper());
-    BCK(cudaMemcpy(b->hyper, h.data(), sizeof(Hyper) * b->n, cudaMemcpyHostToDevice));
-    BCK(cudaMemset(b->status, 0, sizeof(int)));
-    for (BProb& p : b->P) {
-        BCK(cudaMemset(p.ring, 0, (size_t)(p.T + 1) * p.d_pad * 8));
-        BCK(cudaMemset(p.win_sums, 0, (size_t)p.d_pad * 16));
-        BCK(cudaMemset(p.cstat, 0, (size_t)p.d_pad * NCO * 4));
-        launch_fill(p.sigma, 1.0f, p.d_pad, nullptr);
-    }
-    BCK(cudaDeviceSynchronize());
+    b->seed = seed;  // later uploads of the parameter blocks carry it
+    const int blocks = std::min(b->n, 1024);
+    batch_start_kernel<<<blocks, 256, 0, st>>>(b->d_probs, b->hyper, b->n, (uint32_t)seed,
+                                               (uint32_t)(seed >> 32), initial_hyper(), b->status);
+    BCK(cudaGetLastError());
     b->initialized = true;
     return launch(b, 0, 1, st);
 }
@@ -379,15 +409,10 @@ laps_status laps_batch_run(laps_batch* b, int iters_per_launch, void* stream) {
         b->g_iters = iters_per_launch;
     }
     b->last_stream = st;
+    // enough launches for a run that never switches (one step per iteration); a
+    // launch that finds every problem done (or a latched error) returns at once
     const long long max_launches = (long long)b->cfg.n_total_steps / iters_per_launch + 2;
-    for (long long r = 0; r < max_launches; ++r) {
-        BCK(cudaGraphLaunch(b->gexec, st));
-        laps_status s = read_hypers(b);
-        if (s != LAPS_OK) return s;
-        bool all = true;
-        for (int k = 0; k < b->n; ++k) all = all && b->h_hyper[k].done;
-        if (all) return LAPS_OK;
-    }
+    for (long long r = 0; r < max_launches; ++r) BCK(cudaGraphLaunch(b->gexec, st));
     return LAPS_OK;
 }
 
@@ -474,12 +499,11 @@ laps_status laps_batch_get_trace(laps_batch* b, int k, laps_trace_row* rows, int
 laps_status laps_batch_sample(laps_batch* b, int k, float* x_out, void* stream) {
     if (!b || !x_out || k < 0 || k >= b->n || reinterpret_cast<uintptr_t>(x_out) % 4)
         return fail(LAPS_ERR_INVALID_ARG, "bad argument");
-    read_hypers(b);
     const BProb& p = b->P[k];
-    const Hyper& h = b->h_hyper[k];
-    // after a switch that no proposal followed, y is still in x
-    const bool pend = h.phase == 1 && h.p == 0;
-    launch_unpack(p.y, pend ? nullptr : p.sigma, x_out, p.M, (int)p.d, p.d_pad, (cudaStream_t)stream);
+    const int64_t n = p.M * p.d;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    batch_unpack_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(p.y, p.sigma, b->hyper + k, x_out, p.M,
+                                                                  (int)p.d, p.d_pad);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "laps_batch_sample");
 }

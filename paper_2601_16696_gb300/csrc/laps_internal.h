@@ -118,6 +118,9 @@ laps_status status_error(int device_status);
 void stats_from_hyper(const Hyper& h, laps_stats* out);
 void coefs_table(Coefs& cf);
 void launch_fill(float* p, float v, int64_t n, cudaStream_t st);
+// writes the integrator tables with a kernel that takes them by value (stream-ordered,
+// nothing on the host is read after the call returns)
+void launch_set_coefs(Coefs* dst, const Coefs& cf, cudaStream_t st);
 void launch_unpack(const float* src, const float* scale, float* dst, int64_t M, int d, int d_pad,
                    cudaStream_t st);
 }  // namespace laps

@@ -11,10 +11,10 @@
 // so the logits are those of the BF16-rounded data at nearly FP32 accuracy in
 // x and log p stays smooth along a trajectory; R is a single BF16 term.
 //
-// Roles (384 threads): warp 0 loads W once and X / X^T chunks through a
-// 3-stage ring with TMA (128-byte swizzle); warp 1 issues the MMAs from one
-// thread; warps 4..11 are the epilogue (warp w reads TMEM lanes 32 (w % 4) ..
-// +31, i.e. chains, and half of the columns).  All waits are bounded: on
+// Roles (640 threads): warp 0 loads W once and X / X^T chunks through a
+// 4-stage ring with TMA (128-byte swizzle); warp 1 issues the MMAs from one
+// thread; warps 4..19 are the epilogue (warp w reads TMEM lanes 32 (w % 4) ..
+// +31, i.e. chains, and a quarter of the columns).  All waits are bounded: on
 // expiry the CTA records ST_TIMEOUT in the status word, drains what it
 // issued and frees its tensor memory.
 #include <cuda.h>

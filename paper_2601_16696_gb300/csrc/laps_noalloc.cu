@@ -24,7 +24,9 @@ constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // In host code `g_noalloc_scratch` names a host-side stand-in, not a device
-// address; the device address is looked up once per device and cached.
+// address; the device address is looked up once per device and cached.  The
+// cache outlives a cudaDeviceReset, after which the address is stale: this
+// entry point does not support a reset of a device it has run on.
 constexpr int kMaxDevices = 64;
 static void* g_scratch_addr[kMaxDevices];
 static std::mutex g_scratch_mu;
@@ -84,6 +86,12 @@ extern "C" laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M,
                                         const laps_config* cfg, const float* x0, double x0_scale,
                                         uint64_t seed, float* x_out, laps_stats* stats_out,
                                         void* stream) {
+    if (!desc && M == 0 && !cfg && !x_out) {
+        // set-up only: loads the library's device code on the current device (which
+        // reserves the scratch array there) and looks up the array's address
+        void* base = nullptr;
+        return scratch_address(&base);
+    }
     if (!desc || !cfg || !x_out) return fail(LAPS_ERR_INVALID_ARG, "null argument");
     const int64_t d = desc->d;
     if (d < 2 || d > (1 << 24)) return fail(LAPS_ERR_INVALID_ARG, "d must be in [2, 2^24]");
@@ -92,6 +100,10 @@ extern "C" laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M,
         !(cfg->alpha > 0) || !(cfg->C > 0) || cfg->barrier_timeout_ns <= 0)
         return fail(LAPS_ERR_INVALID_ARG, "invalid config value");
     if (cfg->dtilde_K != 0) return fail(LAPS_ERR_UNSUPPORTED, "laps_run_noalloc serves the diagonal bias proxy");
+    if (cfg->precision != LAPS_FP32)
+        return fail(LAPS_ERR_UNSUPPORTED, "laps_run_noalloc computes in FP32 (precision = LAPS_FP32)");
+    if (cfg->stop_b2 > 0)
+        return fail(LAPS_ERR_UNSUPPORTED, "laps_run_noalloc keeps no truth for b^2, so stop_b2 must be 0");
     if ((x0 && reinterpret_cast<uintptr_t>(x0) % 4) || reinterpret_cast<uintptr_t>(x_out) % 4)
         return fail(LAPS_ERR_INVALID_ARG, "x0 and x_out must be 4-byte aligned");
     switch (desc->kind) {
@@ -140,8 +152,9 @@ extern "C" laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M,
     cudaStream_t s = (cudaStream_t)stream;
     Coefs cf;
     coefs_table(cf);
-    cudaError_t e = cudaMemcpyAsync(c.coefs, &cf, sizeof(cf), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy integrator table");
+    launch_set_coefs(c.coefs, cf, s);  // by value: nothing on this stack is read later
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "write integrator table");
     if (t.kind == TGT_GAUSS) {
         e = cudaMemsetAsync(t.prec_pad, 0, (size_t)t.d_pad * 4, s);
         if (e == cudaSuccess)

@@ -417,16 +417,24 @@ def normals(seed: int, m0: int, nm: int, t: int, tag: int, pid: int, d: int,
 def run_noalloc(kind: int, d: int, M: int, x0: torch.Tensor | None, seed: int,
                 out: torch.Tensor, prec: torch.Tensor | None = None, banana_sb: float = 0.1,
                 funnel_sv: float = 3.0, x0_scale: float = 1.0, config: Config | None = None,
-                stream=None, **cfg_kw) -> dict:
+                stream=None, stats: bool = True, **cfg_kw) -> dict | None:
     """One whole LAPS run through laps_run_noalloc (no device allocation in the
-    library); samples are written to ``out`` [M, d].  Returns the final stats."""
+    library); samples are written to ``out`` [M, d].  Returns the final stats
+    (the call then synchronises the stream), or None with ``stats=False`` (the
+    call only enqueues the run)."""
     cfg = config if config is not None else default_config(**cfg_kw)
     desc = TargetDesc(kind, d, prec.data_ptr() if prec is not None else None, banana_sb,
                       funnel_sv, 0, None, None, 1.0)
     s = Stats()
     _check(lib().laps_run_noalloc(C.byref(desc), M, C.byref(cfg), _ptr(x0), x0_scale, seed,
-                                  _ptr(out), C.byref(s), _stream(stream)))
-    return _as_dict(s)
+                                  _ptr(out), C.byref(s) if stats else None, _stream(stream)))
+    return _as_dict(s) if stats else None
+
+
+def noalloc_setup() -> None:
+    """The set-up-only call of laps_run_noalloc: loads its scratch array on the
+    current device and looks up its address, nothing else."""
+    _check(lib().laps_run_noalloc(None, 0, None, None, 0.0, 0, None, None, None))
 
 
 class Batch:
