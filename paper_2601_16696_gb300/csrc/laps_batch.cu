@@ -8,9 +8,12 @@
 // statistics need only sums of y and y^2 per coordinate for this target).
 //
 // A launch runs iterations of Algorithm 1 for every live problem in lockstep:
-//   1. chain phase: every block takes the same share (1/G) of every problem's
-//      chains, so blocks stay balanced whatever phase each problem is in.  A
-//      chain is processed by a group of gw warps (gw = 1..16, chosen per
+//   1. chain phase: a problem's chains are split evenly over a range of
+//      blocks (host-side schedule, batch_schedule): every block when the
+//      problem has at least one group-round of chains per block, else just
+//      enough blocks for one round each, placed where the blocks carry the
+//      least work, so that no block runs a round with most of its groups idle.
+//      A chain is processed by a group of gw warps (gw = 1..16, chosen per
 //      problem from its d), with its coordinates in registers (CPL per lane)
 //      and group reductions by warp butterflies plus, across the group's
 //      warps, shared memory and a named barrier.  Per-coordinate sums of y
@@ -37,11 +40,12 @@ namespace laps {
 
 constexpr int kBT = 512;          // threads per block
 constexpr int kBW = kBT / 32;     // warps per block
-constexpr int kRed = 128;         // reduction scratch floats per group: 2 buffers x 16 warps x 4
+constexpr int kRed = 128;         // reduction scratch floats per group: 2 buffers x 4 values x 16 warps
 
 struct BatchArgs {
     const KParams* probs;  // [n]
     const int* gw;         // [n] warps per chain
+    const int2* sched;     // [n] (first block, blocks) that hold the problem's chains; P.G = blocks
     const Coefs* coefs;
     int n;                 // problems
     int mode;              // 0: initialise, 1: iterate
@@ -52,6 +56,7 @@ struct BatchArgs {
     int* status;
     long long timeout_ns;
     int bar_extra;
+    PhiloxKeys keys;       // round keys of the batch seed (every problem draws with it)
 };
 
 // ---------------------------------------------------------------- chain groups
@@ -69,6 +74,51 @@ __device__ __forceinline__ void grp_bar(const Grp& G) {
     if (G.gw > 1) asm volatile("bar.sync %0, %1;" ::"r"(1 + G.grp), "r"(32 * G.gw) : "memory");
 }
 
+// The group's warps' partials of value k sit at s[16 k + w] (w the warp in the
+// group, gw in {1, 2, 4, 8, 16}); they are read with float4 loads from gw = 4
+// on and added in warp order.
+__device__ __forceinline__ float part_sum(const float* s, int gw) {
+    if (gw < 4) return gw > 1 ? s[0] + s[1] : s[0];
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+    float4 a = s4[0];
+    float t = a.x;
+    t += a.y;
+    t += a.z;
+    t += a.w;
+    for (int q = 1; q < gw / 4; ++q) {
+        a = s4[q];
+        t += a.x;
+        t += a.y;
+        t += a.z;
+        t += a.w;
+    }
+    return t;
+}
+// float-float partials: high words at hi[w], low words at lo[w]
+__device__ __forceinline__ ff part_sum_ff(const float* hi, const float* lo, int gw) {
+    if (gw < 4) {
+        ff t{hi[0], lo[0]};
+        if (gw > 1) t = ff_add(t, ff{hi[1], lo[1]});
+        return t;
+    }
+    const float4* h4 = reinterpret_cast<const float4*>(hi);
+    const float4* l4 = reinterpret_cast<const float4*>(lo);
+    float4 a = h4[0], b = l4[0];
+    ff t{a.x, b.x};
+    t = ff_add(t, ff{a.y, b.y});
+    t = ff_add(t, ff{a.z, b.z});
+    t = ff_add(t, ff{a.w, b.w});
+    for (int q = 1; q < gw / 4; ++q) {
+        a = h4[q];
+        b = l4[q];
+        t = ff_add(t, ff{a.x, b.x});
+        t = ff_add(t, ff{a.y, b.y});
+        t = ff_add(t, ff{a.z, b.z});
+        t = ff_add(t, ff{a.w, b.w});
+    }
+    return t;
+}
+
 // Sum of NV values over the group: warp butterfly, then the group's warps in
 // order.  Two scratch buffers alternate, so one barrier per call suffices (a
 // warp cannot run two calls ahead of the others).  Every lane gets the same bits.
@@ -82,14 +132,10 @@ __device__ __forceinline__ void gsum(Grp& G, float (&v)[NV]) {
     float* s = G.red + G.flip * 64;
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[G.wig * 4 + k] = v[k];
+        for (int k = 0; k < NV; ++k) s[16 * k + G.wig] = v[k];
     grp_bar(G);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        float t = s[k];
-        for (int w = 1; w < G.gw; ++w) t += s[w * 4 + k];
-        v[k] = t;
-    }
+    for (int k = 0; k < NV; ++k) v[k] = part_sum(s + 16 * k, G.gw);
     G.flip ^= 1;
 }
 __device__ __forceinline__ float gsum1(Grp& G, float v) {
@@ -102,12 +148,11 @@ __device__ __forceinline__ ff gsum_ff(Grp& G, ff v) {
     if (G.gw == 1) return v;
     float* s = G.red + G.flip * 64;
     if ((threadIdx.x & 31) == 0) {
-        s[G.wig * 4] = v.hi;
-        s[G.wig * 4 + 1] = v.lo;
+        s[G.wig] = v.hi;
+        s[16 + G.wig] = v.lo;
     }
     grp_bar(G);
-    ff t{s[0], s[1]};
-    for (int w = 1; w < G.gw; ++w) t = ff_add(t, ff{s[w * 4], s[w * 4 + 1]});
+    const ff t = part_sum_ff(s, s + 16, G.gw);
     G.flip ^= 1;
     return t;
 }
@@ -115,14 +160,14 @@ __device__ __forceinline__ ff gsum_ff(Grp& G, ff v) {
 // ---------------------------------------------------------------- maps on a group
 // App. E, Eq. "O update" (Z ~ N(0, I/d) per coordinate; c2s = c2 / sqrt(d))
 template <int CPL>
-__device__ __forceinline__ void g_o(const KParams& P, Grp& G, uint32_t m, uint32_t t, uint32_t tag,
-                                    float c1, float c2s, float (&u)[CPL]) {
+__device__ __forceinline__ void g_o(const KParams& P, const PhiloxKeys& K, Grp& G, uint32_t m, uint32_t t,
+                                    uint32_t tag, float c1, float c2s, float (&u)[CPL]) {
     float n2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         const int j = G.gl + G.lpc * k;
         float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), K, z);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[c]) : 0.0f;
@@ -136,22 +181,23 @@ __device__ __forceinline__ void g_o(const KParams& P, Grp& G, uint32_t m, uint32
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
 }
 
-// The gradient in y of the diagonal Gaussian, g_y = sigma o (-prec o (sigma o y)),
-// for this thread's coordinate block k (recomputed where needed: it is three
-// multiplies, cheaper than keeping it in registers)
+// The gradient in y of the diagonal Gaussian, g_y = sigma o (-prec o (sigma o y))
+// = -c o y with c_i = prec_i sigma_i^2 (kept in shared memory per coordinate),
+// for this thread's coordinate block k (recomputed where needed: one multiply,
+// cheaper than keeping it in registers)
 template <int CPL>
 __device__ __forceinline__ void g_blk(const Grp& G, const KParams& P, const float (&y)[CPL], int k,
-                                      const float4* s_pr4, const float4* s_sg4, float (&g)[4]) {
+                                      const float4* s_c4, float (&g)[4]) {
     const int j = G.gl + G.lpc * k;
     if (j >= P.nblk) {
         g[0] = g[1] = g[2] = g[3] = 0.0f;
         return;
     }
-    const float4 pr = s_pr4[j], sg = s_sg4[j];
-    g[0] = sg.x * (-pr.x * (sg.x * y[4 * k]));
-    g[1] = sg.y * (-pr.y * (sg.y * y[4 * k + 1]));
-    g[2] = sg.z * (-pr.z * (sg.z * y[4 * k + 2]));
-    g[3] = sg.w * (-pr.w * (sg.w * y[4 * k + 3]));
+    const float4 c = s_c4[j];
+    g[0] = -c.x * y[4 * k];
+    g[1] = -c.y * y[4 * k + 1];
+    g[2] = -c.z * y[4 * k + 2];
+    g[3] = -c.w * y[4 * k + 3];
 }
 
 // ---------------------------------------------------------------- fused step
@@ -175,37 +221,32 @@ __device__ __forceinline__ void gsum_mix(Grp& G, ff& a, float (&v)[NV]) {
     if (G.gw == 1) return;
     float* s = G.red + G.flip * 64;
     if ((threadIdx.x & 31) == 0) {
-        s[G.wig * 4] = a.hi;
-        s[G.wig * 4 + 1] = a.lo;
+        s[G.wig] = a.hi;
+        s[16 + G.wig] = a.lo;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[G.wig * 4 + 2 + k] = v[k];
+        for (int k = 0; k < NV; ++k) s[16 * (2 + k) + G.wig] = v[k];
     }
     grp_bar(G);
-    ff t{s[0], s[1]};
-    for (int w = 1; w < G.gw; ++w) t = ff_add(t, ff{s[w * 4], s[w * 4 + 1]});
-    a = t;
+    a = part_sum_ff(s, s + 16, G.gw);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        float x = s[2 + k];
-        for (int w = 1; w < G.gw; ++w) x += s[w * 4 + 2 + k];
-        v[k] = x;
-    }
+    for (int k = 0; k < NV; ++k) v[k] = part_sum(s + 16 * (2 + k), G.gw);
     G.flip ^= 1;
 }
 
 // u <- c1 u + c2s Z, not yet normalised; thread partials of |v|^2 (and, with
 // WITH_G, of g.v and |g|^2 with g the gradient at y) into s
 template <int CPL, bool WITH_G>
-__device__ __forceinline__ void g_o_mix(const KParams& P, const Grp& G, uint32_t m, uint32_t t, uint32_t tag,
+__device__ __forceinline__ void g_o_mix(const KParams& P, const PhiloxKeys& K, const Grp& G, uint32_t m,
+                                        uint32_t t, uint32_t tag,
                                         float c1, float c2s, float (&u)[CPL], const float (&y)[CPL],
-                                        const float4* s_pr4, const float4* s_sg4, float (&s)[3]) {
+                                        const float4* s_c4, float (&s)[3]) {
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         const int j = G.gl + G.lpc * k;
         float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+        if (j < P.nblk) normals4(j, m, t, tag | (P.pid << 8), K, z);
         float g[4];
-        if (WITH_G) g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
+        if (WITH_G) g_blk<CPL>(G, P, y, k, s_c4, g);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float v = (4 * j + c < P.d) ? fmaf(c1, u[4 * k + c], c2s * z[c]) : 0.0f;
@@ -223,7 +264,7 @@ __device__ __forceinline__ void g_o_mix(const KParams& P, const Grp& G, uint32_t
 template <int CPL>
 __device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float beps, float inv_dm1, float dm1,
                                           float gg, float gu, const float (&y)[CPL], float (&u)[CPL], ff& dl,
-                                          const float4* s_pr4, const float4* s_sg4) {
+                                          const float4* s_c4) {
     if (!(gg > 0.0f)) return;
     // per-chain scalars as in the resident kernel's B: 1/|g| from one reciprocal
     // square root, zeta from 1 - zeta, the positive denominator inverted approximately
@@ -241,7 +282,7 @@ __device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float 
 #pragma unroll
     for (int k = 0; k < CPL / 4; ++k) {
         float g[4];
-        g_blk<CPL>(G, P, y, k, s_pr4, s_sg4, g);
+        g_blk<CPL>(G, P, y, k, s_c4, g);
 #pragma unroll
         for (int c = 0; c < 4; ++c) u[4 * k + c] = fmaf(cu, u[4 * k + c], ce * g[c]);
     }
@@ -249,20 +290,20 @@ __device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float 
 }
 
 template <int CPL>
-__device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF, int integ, float eps, float c1,
-                                       float c2s, uint32_t m, uint32_t t, float (&y)[CPL], float (&u)[CPL], ff& dl,
-                                       float inv_dm1, float dm1, const float4* s_pr4, const float4* s_sg4,
+__device__ __forceinline__ void g_step(const KParams& P, const PhiloxKeys& RK, Grp& G, const Coefs& CF, int integ,
+                                       float eps, float c1, float c2s, uint32_t m, uint32_t t, float (&y)[CPL],
+                                       float (&u)[CPL], ff& dl, float inv_dm1, float dm1, const float4* s_c4,
                                        bool check, bool& bad) {
     const int K = CF.K[integ];
     float s[3] = {0.0f, 0.0f, 0.0f};
-    g_o_mix<CPL, true>(P, G, m, t, TAG_O1, c1, c2s, u, y, s_pr4, s_sg4, s);
+    g_o_mix<CPL, true>(P, RK, G, m, t, TAG_O1, c1, c2s, u, y, s_c4, s);
     gsum<3>(G, s);
     float inv = s[0] > 0.0f ? rsqrtf(s[0]) : 0.0f;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) u[q] *= inv;
     float gg = s[2], gu = s[1] * inv;
     for (int k = 0; k < K; ++k) {
-        g_b_apply<CPL>(G, P, CF.b[integ][k] * eps, inv_dm1, dm1, gg, gu, y, u, dl, s_pr4, s_sg4);
+        g_b_apply<CPL>(G, P, CF.b[integ][k] * eps, inv_dm1, dm1, gg, gu, y, u, dl, s_c4);
         if (k < K - 1) {
             // A map, its log p change (difference form) and the next B's sums
             const float ae = CF.a[integ][k] * eps;
@@ -271,17 +312,17 @@ __device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF
             for (int kb = 0; kb < CPL / 4; ++kb) {
                 const int j = G.gl + G.lpc * kb;
                 if (j >= P.nblk) continue;
-                const float4 pr4 = s_pr4[j], sg4 = s_sg4[j];
-                const float prs[4] = {pr4.x, pr4.y, pr4.z, pr4.w}, sgs[4] = {sg4.x, sg4.y, sg4.z, sg4.w};
+                const float4 c4 = s_c4[j];
+                const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
+                    // log p(y') - log p(y) = -1/2 c (y' - y)(y' + y)
                     const int q = 4 * kb + c;
-                    const float xo = sgs[c] * y[q];
-                    const float yn = fmaf(ae, u[q], y[q]);
-                    const float xn = sgs[c] * yn;
-                    part = fmaf(-0.5f * prs[c] * (xn - xo), xo + xn, part);
+                    const float yo = y[q];
+                    const float yn = fmaf(ae, u[q], yo);
+                    part = fmaf(-0.5f * cs[c] * (yn - yo), yo + yn, part);
                     y[q] = yn;
-                    const float g = sgs[c] * (-prs[c] * xn);
+                    const float g = -cs[c] * yn;
                     v2[0] = fmaf(g, g, v2[0]);
                     v2[1] = fmaf(g, u[q], v2[1]);
                 }
@@ -294,7 +335,7 @@ __device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF
         }
     }
     float s2[3] = {0.0f, 0.0f, 0.0f};
-    g_o_mix<CPL, false>(P, G, m, t, TAG_O2, c1, c2s, u, y, s_pr4, s_sg4, s2);
+    g_o_mix<CPL, false>(P, RK, G, m, t, TAG_O2, c1, c2s, u, y, s_c4, s2);
     if (check) {
         float f = isfinite(dl.hi) ? 0.0f : 1.0f;
 #pragma unroll
@@ -314,7 +355,7 @@ __device__ __forceinline__ void g_step(const KParams& P, Grp& G, const Coefs& CF
 
 // ---------------------------------------------------------------- the kernel
 template <int CPL>
-__global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
+__global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ BatchArgs B) {
     constexpr int NB = CPL / 4;
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ KParams sP;
@@ -324,8 +365,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
     __shared__ float s_eps, s_c1, s_c2s;
     __shared__ int s_live;
     float* qbuf = reinterpret_cast<float*>(bsm);   // [2][ng][lpc CPL]: per-thread column sums
-    float* s_pr = qbuf + 2 * kBT * CPL;            // [cap_pad] precisions
-    float* s_sg = s_pr + B.cap_pad;                // [cap_pad] preconditioner
+    float* s_c = qbuf + 2 * kBT * CPL;             // [cap_pad] prec_i sigma_i^2 (0 past d)
+    float* s_sg = s_c + B.cap_pad;                 // [cap_pad] preconditioner
     float* s_red = s_sg + B.cap_pad;               // [kBW][kRed]
     ff* s_cs = reinterpret_cast<ff*>(s_red + kBW * kRed);  // [kBW][NCS]
     ff* s_q = s_cs + kBW * NCS;                    // [NQ SL + NCS]
@@ -343,7 +384,6 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
         __syncthreads();
         if (tid == 0) {
             sP.mode = B.mode;
-            sP.G = G;
             sH = *sP.hyper;
             set_step_scalars(sH, sP.d, s_eps, s_c1, s_c2s);
         }
@@ -364,12 +404,16 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
         if (!s_live) break;  // uniform: every block reads the same phase machines
         // ------------------------------------------------ 1. chain phase
         for (int p = 0; p < B.n; ++p) {
+            const int2 sc = B.sched[p];  // the same for every thread: a uniform branch
+            const int slot = b - sc.x;
+            if (slot < 0 || slot >= sc.y) continue;
             load_prob(p);
             if (B.mode == 1 && sH.done) continue;
             const KParams& P = sP;
             for (int i = tid; i < P.d_pad; i += kBT) {
-                s_pr[i] = i < P.d ? P.prec[i] : 0.0f;
-                s_sg[i] = P.sigma[i];
+                const float sg = P.sigma[i];
+                s_c[i] = i < P.d ? P.prec[i] * (sg * sg) : 0.0f;
+                s_sg[i] = sg;
             }
             const int gw = B.gw[p], ng = kBW / gw;
             Grp Gc{gw, warp / gw, warp % gw, (warp % gw) * 32 + lane, 32 * gw, s_red + (warp / gw) * kRed, 0};
@@ -377,8 +421,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
             // this thread's column slots, one float4 per coordinate block (conflict-free)
             float4* q0 = reinterpret_cast<float4*>(qbuf + (size_t)(0 * ng + Gc.grp) * cap);
             float4* q1 = reinterpret_cast<float4*>(qbuf + (size_t)(1 * ng + Gc.grp) * cap);
-            const float4* s_pr4 = reinterpret_cast<const float4*>(s_pr);
-            const float4* s_sg4 = reinterpret_cast<const float4*>(s_sg);
+            const float4* s_c4 = reinterpret_cast<const float4*>(s_c);
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 const int j = Gc.gl + Gc.lpc * k;
@@ -392,7 +435,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
             const float eps = s_eps, c1 = s_c1, c2s = s_c2s;
             const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
             const bool pend = (B.mode == 1 && sH.phase == 1 && sH.p == 0);  // y still in x (switch)
-            const int64_t m0 = (int64_t)b * P.M / G, m1 = (int64_t)(b + 1) * P.M / G;
+            const int64_t m0 = (int64_t)slot * P.M / sc.y, m1 = (int64_t)(slot + 1) * P.M / sc.y;
             for (int64_t mm = m0 + Gc.grp; mm < m1; mm += ng) {
                 const uint32_t m = (uint32_t)mm;
                 float y[CPL], u[CPL];
@@ -421,7 +464,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                         const int j = Gc.gl + Gc.lpc * k;
                         float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                         if (j < P.nblk && P.x0 == nullptr)
-                            normals4(j, m, 0u, TAG_X0 | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+                            normals4(j, m, 0u, TAG_X0 | (P.pid << 8), B.keys, z);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = 4 * j + c;
@@ -435,7 +478,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
 #pragma unroll
                     for (int k = 0; k < NB; ++k) {
                         float g[4];
-                        g_blk<CPL>(Gc, P, y, k, s_pr4, s_sg4, g);
+                        g_blk<CPL>(Gc, P, y, k, s_c4, g);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             n2 = fmaf(g[c], g[c], n2);
@@ -445,13 +488,13 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                     n2 = gsum1(Gc, n2);
 #pragma unroll
                     for (int q = 0; q < CPL; ++q) u[q] = 0.0f;
-                    g_o<CPL>(P, Gc, m, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
+                    g_o<CPL>(P, B.keys, Gc, m, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
                     if (n2 > 0.0f) {
                         const float inv = 1.0f / sqrtf(n2);
 #pragma unroll
                         for (int k = 0; k < NB; ++k) {
                             float g[4];
-                            g_blk<CPL>(Gc, P, y, k, s_pr4, s_sg4, g);
+                            g_blk<CPL>(Gc, P, y, k, s_c4, g);
 #pragma unroll
                             for (int c = 0; c < 4; ++c) u[4 * k + c] = g[c] * inv;
                         }
@@ -474,8 +517,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                     const int integ = sH.phase == 0 ? INTEG_LF : sH.integ;
                     bool bad = false;
                     if (sH.phase == 0) {
-                        g_step<CPL>(P, Gc, CF, integ, eps, c1, c2s, m, (uint32_t)sH.t, y, u, dl, inv_dm1, dm1,
-                                    s_pr4, s_sg4, true, bad);
+                        g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, (uint32_t)sH.t, y, u, dl, inv_dm1, dm1,
+                                    s_c4, true, bad);
                     } else {
                         // App. F step 2: u uniform on the sphere, then N steps
                         float n2 = 0.0f;
@@ -484,7 +527,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                             const int j = Gc.gl + Gc.lpc * k;
                             float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                             if (j < P.nblk)
-                                normals4(j, m, (uint32_t)sH.p, TAG_REFRESH | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+                                normals4(j, m, (uint32_t)sH.p, TAG_REFRESH | (P.pid << 8), B.keys, z);
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const float v = (4 * j + c < P.d) ? z[c] : 0.0f;
@@ -498,15 +541,15 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                         for (int q = 0; q < CPL; ++q) u[q] *= inv;
                         const uint32_t t0 = (uint32_t)sH.t;
                         for (int n = 0; n < P.N; ++n)
-                            g_step<CPL>(P, Gc, CF, integ, eps, c1, c2s, m, t0 + n, y, u, dl, inv_dm1, dm1, s_pr4,
-                                        s_sg4, n == P.N - 1, bad);
+                            g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, t0 + n, y, u, dl, inv_dm1, dm1, s_c4,
+                                        n == P.N - 1, bad);
                     }
                     bool keep = !bad;
                     float a_m = 0.0f;
                     if (sH.phase == 1) {
                         // App. F step 5: accept with probability min(1, e^-Delta)
                         const uint4 r = philox4x32_10(
-                            make_uint4(0u, m, (uint32_t)sH.p, TAG_MH | (P.pid << 8)), P.seed_lo, P.seed_hi);
+                            make_uint4(0u, m, (uint32_t)sH.p, TAG_MH | (P.pid << 8)), B.keys);
                         const ff s = ff_add(dl, logf(u01(r.x)));
                         keep = !bad && (s.hi < 0.0f || (s.hi == 0.0f && s.lo < 0.0f));
                         a_m = bad ? 0.0f : (dl.hi <= 0.0f ? 1.0f : expf(-(dl.hi + dl.lo)));
@@ -564,12 +607,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const BatchArgs B) {
                     const float* src = qbuf + (size_t)q * ng * cap + i;
                     ff s = ff_make(src[0]);
                     for (int gg = 1; gg < ng; ++gg) s = ff_add(s, src[(size_t)gg * cap]);
-                    P.part[((size_t)q * dp + i) * G2 + b] = make_float2(s.hi, s.lo);
+                    P.part[((size_t)q * dp + i) * G2 + slot] = make_float2(s.hi, s.lo);
                 }
             if (tid < NCS) {
                 ff s = s_cs[tid];
                 for (int gg = 1; gg < ng; ++gg) s = ff_add(s, s_cs[gg * NCS + tid]);
-                P.part[((size_t)NQ * dp + tid) * G2 + b] = make_float2(s.hi, s.lo);
+                P.part[((size_t)NQ * dp + tid) * G2 + slot] = make_float2(s.hi, s.lo);
             }
         }
         // ------------------------------------------------ 2. slices
@@ -637,12 +680,14 @@ int batch_gw(int64_t d, int cpl, int widen) {
     return gw;
 }
 
-cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const Coefs* coefs, int n,
-                         int mode, int n_iters, int SL, int cap_pad, unsigned* bar, int* status,
-                         long long timeout_ns, int bar_extra, cudaStream_t st) {
+cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const int2* sched,
+                         const Coefs* coefs, int n, int mode, int n_iters, int SL, int cap_pad, unsigned* bar,
+                         int* status, long long timeout_ns, int bar_extra, uint64_t seed, cudaStream_t st) {
     BatchArgs a;
+    a.keys = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
     a.probs = probs;
     a.gw = gw;
+    a.sched = sched;
     a.coefs = coefs;
     a.n = n;
     a.mode = mode;
@@ -678,6 +723,57 @@ cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, co
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+// A block runs one problem at a time with all its ng = 16 / gw chain groups; a
+// round (ng chains side by side) costs about ceil(nblk / (32 gw)) passes over
+// the lanes' coordinate blocks whatever gw is, so that is a problem's cost per
+// round.  A problem with at least ng chains per block is spread over every
+// block (rounds = ceil(ceil(M / G) / ng) each).  Any other problem gets
+// ceil(M / ng) blocks, one round each, at the place where the most loaded of
+// those blocks carries the least work so far (larger problems placed first).
+void batch_schedule(const int64_t* d, const int64_t* M, int n, int cpl, int widen, int G, int2* sched) {
+    std::vector<double> load(G, 0.0);
+    std::vector<int> order;
+    auto cost = [&](int k, int& ng) {
+        const int gw = batch_gw(d[k], cpl, widen);
+        ng = kBW / std::max(gw, 1);
+        const int64_t nblk = (d[k] + 3) / 4;
+        return (double)((nblk + 32 * gw - 1) / (32 * gw));
+    };
+    for (int k = 0; k < n; ++k) {
+        int ng = 1;
+        const double c = cost(k, ng);
+        if (M[k] >= (int64_t)G * ng) {
+            sched[k] = make_int2(0, G);
+            const double rounds = (double)((((M[k] + G - 1) / G) + ng - 1) / ng);
+            for (int b = 0; b < G; ++b) load[b] += rounds * c;
+        } else {
+            order.push_back(k);
+        }
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        int na = 1, nb = 1;
+        const double ca = cost(a, na), cb = cost(b, nb);
+        return ca * (double)((M[a] + na - 1) / na) > cb * (double)((M[b] + nb - 1) / nb);
+    });
+    for (int k : order) {
+        int ng = 1;
+        const double c = cost(k, ng);
+        const int nb = (int)std::min<int64_t>(G, std::max<int64_t>(1, (M[k] + ng - 1) / ng));
+        int best = 0;
+        double best_max = 1e300;
+        for (int b0 = 0; b0 + nb <= G; ++b0) {
+            double mx = 0.0;
+            for (int b = b0; b < b0 + nb; ++b) mx = std::max(mx, load[b]);
+            if (mx < best_max) {
+                best_max = mx;
+                best = b0;
+            }
+        }
+        sched[k] = make_int2(best, nb);
+        for (int b = best; b < best + nb; ++b) load[b] += c;
+    }
 }
 
 int batch_blocks_per_sm(int cpl, int cap_pad, int SL) {

@@ -49,6 +49,8 @@ struct laps_batch {
     Hyper* h_hyper = nullptr;    // [n] pinned host copy
     KParams* d_probs = nullptr;  // [n] parameter blocks the kernel reads
     int* d_gw = nullptr;         // [n] warps per chain
+    int2* d_sched = nullptr;     // [n] blocks that hold each problem's chains
+    std::vector<int2> sched;     // host copy
     Coefs* d_coefs = nullptr;
     unsigned* bar = nullptr;
     int* status = nullptr;
@@ -60,6 +62,7 @@ struct laps_batch {
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture
     cudaGraphExec_t gexec = nullptr;
     int g_iters = 0;
+    uint64_t g_seed = 0;
 };
 
 namespace {
@@ -120,7 +123,7 @@ KParams make_params(const laps_batch* b, int k) {
     P.seed_lo = (uint32_t)b->seed;
     P.seed_hi = (uint32_t)(b->seed >> 32);
     P.pid = (uint32_t)k;
-    P.G = b->G;
+    P.G = b->sched.empty() ? b->G : b->sched[k].y;  // columns the slice owners add
     P.qpp = 1;
     P.smax = b->SL;
     P.bar_extra = g.barrier_extra_arrivals;
@@ -129,6 +132,13 @@ KParams make_params(const laps_batch* b, int k) {
 }
 
 laps_status upload(laps_batch* b) {
+    std::vector<int64_t> dd(b->n), mm(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        dd[k] = b->P[k].d;
+        mm[k] = b->P[k].M;
+    }
+    b->sched.assign(b->n, make_int2(0, 0));
+    batch_schedule(dd.data(), mm.data(), b->n, b->cpl, b->widen, b->G, b->sched.data());
     std::vector<KParams> h(b->n);
     std::vector<int> gw(b->n);
     for (int k = 0; k < b->n; ++k) {
@@ -138,6 +148,7 @@ laps_status upload(laps_batch* b) {
     }
     BCK(cudaMemcpy(b->d_probs, h.data(), sizeof(KParams) * b->n, cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_gw, gw.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_sched, b->sched.data(), sizeof(int2) * b->n, cudaMemcpyHostToDevice));
     return LAPS_OK;
 }
 
@@ -156,9 +167,9 @@ laps_status set_shape(laps_batch* b, int cpl, int widen, int SL) {
 }
 
 laps_status launch(laps_batch* b, int mode, int n_iters, cudaStream_t st) {
-    cudaError_t e = batch_launch(b->cpl, b->G, b->d_probs, b->d_gw, b->d_coefs, b->n, mode, n_iters, b->SL,
-                                 b->cap_pad, b->bar, b->status, b->cfg.barrier_timeout_ns,
-                                 b->cfg.barrier_extra_arrivals, st);
+    cudaError_t e = batch_launch(b->cpl, b->G, b->d_probs, b->d_gw, b->d_sched, b->d_coefs, b->n, mode, n_iters,
+                                 b->SL, b->cap_pad, b->bar, b->status, b->cfg.barrier_timeout_ns,
+                                 b->cfg.barrier_extra_arrivals, b->seed, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_kernel launch");
     b->last_stream = st;
     return LAPS_OK;
@@ -294,7 +305,8 @@ laps_status laps_batch_create(const laps_problem* probs, int n, const laps_confi
         return fail(LAPS_ERR_UNSUPPORTED, "no batch shape holds these problems");
     }
     bool ok = alloc((void**)&b->hyper, sizeof(Hyper) * n) && alloc((void**)&b->d_probs, sizeof(KParams) * n) &&
-              alloc((void**)&b->d_gw, sizeof(int) * n) && alloc((void**)&b->d_coefs, sizeof(Coefs)) &&
+              alloc((void**)&b->d_gw, sizeof(int) * n) && alloc((void**)&b->d_sched, sizeof(int2) * n) &&
+              alloc((void**)&b->d_coefs, sizeof(Coefs)) &&
               alloc((void**)&b->bar, 4 * sizeof(unsigned)) && alloc((void**)&b->status, sizeof(int));
     for (int k = 0; k < n && ok; ++k) {
         BProb& p = b->P[k];
@@ -389,7 +401,8 @@ laps_status laps_batch_run(laps_batch* b, int iters_per_launch, void* stream) {
     if (!b || iters_per_launch < 1) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (!b->initialized) return fail(LAPS_ERR_INVALID_ARG, "laps_batch_init has not run");
     cudaStream_t st = (cudaStream_t)stream;
-    if (!b->gexec || b->g_iters != iters_per_launch) {
+    // the launch carries the seed's Philox round keys: a new seed needs a new graph
+    if (!b->gexec || b->g_iters != iters_per_launch || b->g_seed != b->seed) {
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);
             b->gexec = nullptr;
@@ -407,6 +420,7 @@ laps_status laps_batch_run(laps_batch* b, int iters_per_launch, void* stream) {
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "instantiating the batch graph");
         b->g_iters = iters_per_launch;
+        b->g_seed = b->seed;
     }
     b->last_stream = st;
     // enough launches for a run that never switches (one step per iteration); a

@@ -33,6 +33,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The ten round keys of key (k0, k1): round r xors with (k0 + r W0, k1 + r W1)
+// (the Weyl increments above).  A kernel that takes them as a parameter finds
+// them in the constant bank, so a round needs no key additions.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+__host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        K.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+        c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // ((r >> 9) + 1/2) 2^-23 = (r >> 9) 2^-23 + 2^-24: a binary32 value in (0, 1), exact
 // (one fused multiply-add of exact terms).
 __device__ __forceinline__ float u01(uint32_t r) {
@@ -57,6 +83,21 @@ __device__ __forceinline__ void cos_sin_2pi(float u, float& c, float& s) {
 }
 
 // Four standard normals for coordinates 4j..4j+3 (Box-Muller on (r0,r1), (r2,r3)).
+__device__ __forceinline__ void box_muller4(const uint4 r, float z[4]) {
+    float s, c;
+    float rad = bm_radius(u01(r.x));
+    cos_sin_2pi(u01(r.y), c, s);
+    z[0] = rad * c;
+    z[1] = rad * s;
+    rad = bm_radius(u01(r.z));
+    cos_sin_2pi(u01(r.w), c, s);
+    z[2] = rad * c;
+    z[3] = rad * s;
+}
+__device__ __forceinline__ void normals4(uint32_t j, uint32_t m, uint32_t t, uint32_t tagpid,
+                                         const PhiloxKeys& K, float z[4]) {
+    box_muller4(philox4x32_10(make_uint4(j, m, t, tagpid), K), z);
+}
 __device__ __forceinline__ void normals4(uint32_t j, uint32_t m, uint32_t t, uint32_t tagpid,
                                          uint32_t k0, uint32_t k1, float z[4]) {
     const uint4 r = philox4x32_10(make_uint4(j, m, t, tagpid), k0, k1);

@@ -91,9 +91,12 @@ size_t batch_smem(int cpl, int cap_pad, int SL);
 int batch_threads();
 int batch_gw(int64_t d, int cpl, int widen);
 int batch_blocks_per_sm(int cpl, int cap_pad, int SL);
-cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const Coefs* coefs, int n,
-                         int mode, int n_iters, int SL, int cap_pad, unsigned* bar, int* status,
-                         long long timeout_ns, int bar_extra, cudaStream_t st);
+cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const int2* sched,
+                         const Coefs* coefs, int n, int mode, int n_iters, int SL, int cap_pad, unsigned* bar,
+                         int* status, long long timeout_ns, int bar_extra, uint64_t seed, cudaStream_t st);
+// Blocks that hold each problem's chains: sched[k] = (first block, blocks) for
+// problems of dimension d[k] and M[k] chains on G blocks of the shape (cpl, widen).
+void batch_schedule(const int64_t* d, const int64_t* M, int n, int cpl, int widen, int G, int2* sched);
 // streamed path (laps_streamed.cu)
 laps_status streamed_setup(laps_ctx* c);
 laps_status streamed_alloc(laps_ctx* c);
