@@ -67,3 +67,48 @@ def test_logreg_truth_attached_on_request():
     pr = W.logreg(n_data=300, n_feat=5, M=4, n_steps=1, with_truth=True)
     assert pr.Ex2.shape == (6,) and np.all(pr.Varx2 > 0)
     assert W.logreg(n_data=300, n_feat=5, M=4, n_steps=1).Ex2 is None
+
+
+def _importance():
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_logreg_moments.py")
+    spec = importlib.util.spec_from_file_location("make_logreg_moments", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("n_data", [500, 4000])
+def test_importance_moments_against_integration(ora, n_data):
+    """The importance-sampling estimator behind the stored logistic-regression
+    moments reproduces the brute-force integral of a 2-D posterior within its
+    own standard error."""
+    pr = W.logreg(n_data=n_data, n_feat=1, M=4, n_steps=1, data_seed=3)
+    ex2, var2, _, _ = _grid_moments(ora, pr)
+    iex2, ivar2, se, ess = _importance().importance_moments(pr.X, pr.y, pr.prior_var, 40000)
+    assert ess > 30000
+    assert np.all(np.abs(iex2 - ex2) < 5.0 * se), ((iex2 - ex2) / se)
+    np.testing.assert_allclose(ivar2, var2, rtol=0.05)
+
+
+def test_logreg_reference_moments_file():
+    """The stored reference moments of the full-size workload: the effective
+    sample size and Monte Carlo error it states, and its Laplace column equal
+    to the workload's own Laplace moments (the same data)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "logreg_d101_n10000_moments.txt")
+    import re
+    head = " ".join(line for line in open(path) if line.startswith("#"))
+    ess = float(re.search(r"effective sample size (\d+)", head).group(1))
+    assert ess > 1e5
+    a = np.loadtxt(path)
+    assert a.shape == (101, 5) and np.array_equal(a[:, 0], np.arange(101))
+    ex2, var2, se, lap = a[:, 1], a[:, 2], a[:, 3], a[:, 4]
+    assert np.all(var2 > 0) and np.all(se / np.sqrt(var2) < 0.01)
+    pr = W.logreg(with_truth=True)
+    np.testing.assert_allclose(lap, pr.Ex2, rtol=1e-12)
+    truth = W.logreg_reference_moments()
+    np.testing.assert_array_equal(truth[0], ex2)
+    np.testing.assert_array_equal(truth[1], var2)
