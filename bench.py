@@ -1,23 +1,37 @@
 """Benchmark of the LAPS hot path on GB300: one JSON line on stdout.
 
 A step is one complete LAPS run (Algorithm 1: initialisation, the unadjusted
-phase, the switch, the adjusted phase, the samples) of the workload: the
-banana target, d = 100, M = 4096 chains, 5000 integrator steps.  The paper's
-default switch rule would keep this ensemble unadjusted (its window statistic
-stays above 0.01 at M = 4096), so the timed runs switch after the first window
-(1000 steps, the paper's "number of unadjusted steps" ablation knob) and run
-MAMS proposals for the remaining 4000 steps.
+phase, the switch, the adjusted phase, the samples) of the batched workload:
+64 independent diagonal Gaussians of uneven dimension (d log-uniform in
+[10, 2000], condition number log-uniform in [1e2, 1e4], 512..4096 chains) plus
+one d = 10^4 Gaussian with 16384 chains, 234.6 M coordinates in all, every
+problem 2000 integrator steps, all in one persistent launch per graph replay.
+The paper's switch rule does not fire at these ensemble sizes (its window
+statistic stays above 0.01), so the timed runs switch at the first full window
+(step 400, the paper's "number of unadjusted steps" ablation knob) and run
+MAMS proposals (MN2 for d <= 200, MN4 above) for the remaining steps.
 
-value      chain-gradient-evals/s = M x gradient evaluations per chain / time,
-           inputs resident on the device, CUDA events on the launching stream.
-e2e        the same metric through the public API with host buffers: x0 copied
-           from pinned host memory and the samples copied back in the timed
+value      chain-gradient-evals/s = sum over problems of M x gradient
+           evaluations per chain / time of the whole run (laps_batch_init +
+           laps_batch_run), initial positions resident on the device, CUDA
+           events on the launching stream.  The state (1.9 GB) is larger than
+           L2, so no flush is needed between runs.
+e2e        the same metric through the batch entry points with host buffers:
+           the initial positions copied in from pinned host memory, every
+           problem's samples (laps_batch_sample) copied back, inside the timed
            region.
-time_to_b2 wall time (CUDA events) of runs that stop at b^2_max < 0.01.
-roofline   the persistent kernel against the FP32 ALU issue rate: algorithmic
-           operations of the run (the per-coordinate counts below) over the
-           kernel's own duration, against SMs x 128 lanes x the measured clock.
+time_to_b2 per run, the device time from laps_batch_init until every problem's
+           b^2_avg (Eq. "bias", against the closed-form moments) is below 0.01.
+roofline   batch_kernel against the FP32 ALU issue rate: algorithmic operations
+           of the run (the per-coordinate counts below) over the kernel's own
+           duration (CUDA events around every launch of a whole run), against
+           SMs x 128 lanes x the measured clock; beside it the counted
+           instructions (ncu) and the algorithmic HBM bytes.
 cpu_baseline  the FP64 oracle on the host cores on a bounded sample.
+
+The register-resident form (banana d = 100, M = 4096, 5000 steps), the
+logistic regression in its precisions, the ill-conditioned Gaussian and the
+full-rank proxy are measured in the same run and reported under "forms".
 
 --impl reference runs the oracle (the only reference this path has) instead.
 """
@@ -41,13 +55,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "chain-gradient-evals/sec and wall time to second-moment bias^2<0.01, 1 GB300"
 UNIT = "chain-grad-evals/s"
-WORKLOAD = dict(name="banana_d100", d=100, M=4096, n_steps=5000, switch_at=1000)
-# algorithmic ALU operations per coordinate and gradient evaluation: an LF
-# unadjusted step (two O maps: a quarter Philox4x32-10 call, half a Box-Muller
-# pair, uniforms and the O arithmetic, 48 each; two B maps, the A map with the
-# target and the ensemble sums, 21) and an MN2 adjusted step per gradient
-ALU_OPS_LF = 117.0
-ALU_OPS_MN2_PER_GRAD = 61.0
+BATCH = dict(name="batch64", n_steps=2000, switch_at=400, iters_per_launch=64)
+RESIDENT = dict(name="banana_d100", d=100, M=4096, n_steps=5000, switch_at=1000)
+# Algorithmic ALU operations per coordinate (one FP32 lane operation each):
+# an O map is 48 (a quarter Philox4x32-10 call ~25 integer operations, half a
+# Box-Muller pair ~17, uniforms 3, the O arithmetic 3), a B map 4, an A map
+# with the target's gradient and log-p change 7 (banana and diagonal Gaussian
+# alike), the ensemble sums 6 per step (y, y^2, g, y g) in the resident kernel
+# and 2 (y, y^2) in the batch.
+OPS_O, OPS_B, OPS_A = 48.0, 4.0, 7.0
+ALU_OPS_LF = 2 * OPS_O + 2 * OPS_B + OPS_A + 6.0            # resident: 117 per step (1 gradient)
+ALU_OPS_MN2_PER_GRAD = (2 * OPS_O + 3 * OPS_B + 2 * OPS_A) / 2  # 61
+BATCH_OPS_LF = 2 * OPS_O + 2 * OPS_B + OPS_A + 2.0          # 113 per step (1 gradient)
+BATCH_OPS_STEP = {1: 2 * OPS_O + 3 * OPS_B + 2 * OPS_A,     # MN2: 122 per step (2 gradients)
+                  2: 2 * OPS_O + 6 * OPS_B + 5 * OPS_A}     # MN4: 155 per step (5 gradients)
 
 
 def _rank_env():
@@ -115,29 +136,39 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def _kernel_source_hash() -> str:
+RESIDENT_SRC = ("laps_resident_kernel.cuh", "laps_resident.cuh", "laps_finalise.cuh", "laps_device.cuh",
+                "laps_params.h")
+BATCH_SRC = ("laps_batch.cu", "laps_resident.cuh", "laps_finalise.cuh", "laps_device.cuh", "laps_params.h")
+
+
+def _kernel_source_hash(files=RESIDENT_SRC) -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_16696_gb300", "csrc")
-    for f in ("laps_resident_kernel.cuh", "laps_resident.cuh", "laps_finalise.cuh", "laps_device.cuh",
-              "laps_params.h"):
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the ncu capture in profiles/, or None when the
-    kernel sources changed after that capture."""
-    path = os.path.join(ROOT, "profiles", "resident_traffic.txt")
+def _recorded(kernel: str, name: str = "resident_traffic.txt", files=RESIDENT_SRC):
+    """The figures recorded for `kernel` in profiles/<name> from one ncu
+    capture, or None when the kernel sources changed after that capture."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    cur = _kernel_source_hash()
+    cur = _kernel_source_hash(files)
     for line in open(path):
         f = line.split()
         if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == cur:
-            return float(f[2])
+            return [float(v) for v in f[2:]]
     return None
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch of the resident kernel (profiles/resident_traffic.txt)."""
+    r = _recorded(kernel)
+    return r[0] if r else None
 
 
 def _cpu_baseline(pr, seconds_hint=True, single_thread=False, grads_to_b2=None):
@@ -242,25 +273,61 @@ def _probe_peaks(stream):
     return out
 
 
+def _batch_config(probs, extra=None):
+    coords = sum(p.d * p.M for p in probs)
+    cfg = {"workload": "batch64: 64 diagonal Gaussians, d log-uniform in [10, 2000], condition "
+                       "1e2..1e4, M in {512..4096}, + d=10000 M=16384; %d steps each" % BATCH["n_steps"],
+           "problems": len(probs), "coordinates": coords, "chains": sum(p.M for p in probs),
+           "switch": "after %d unadjusted steps (the first full window; the paper's rule does not "
+                     "fire at these ensemble sizes)" % BATCH["switch_at"],
+           "l2": "not flushed: the state (%.1f GB) is larger than L2" % (8.0 * coords / 1e9)}
+    cfg.update(extra or {})
+    return cfg
+
+
+def _batch_oracle(probs, total_chain_grads=None):
+    """The oracle, as it stands, on all host cores on a bounded sample of the
+    batch: one unadjusted iteration (one gradient per chain) of each of the 64
+    small problems with all their chains, and of the d = 10^4 problem on its
+    first 1024 chains.  total_chain_grads (the GPU run's) adds the oracle's
+    projected time for a whole run."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    evals, dt = 0, 0.0
+    for k, pr in enumerate(probs):
+        if pr.d >= 10000:
+            pr = dataclasses.replace(pr, M=1024, x0=pr.x0[:1024])
+        tg = oracle.OracleTarget(pr.kind, pr.d, prec=pr.prec)
+        run = oracle.OracleLAPS(tg, pr.x0, seed=0, pid=k, n_total_steps=pr.n_steps)
+        t0 = time.perf_counter()
+        run.iterate(1)
+        dt += time.perf_counter() - t0
+        evals += pr.M * (run.trace[-1]["grads"] - 1)
+    v = evals / dt
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+           "sample": "FP64 oracle, one unadjusted iteration of the 64 small problems (all chains) "
+                     "and of the d = 10^4 problem on 1024 of its chains: %d chain-gradient "
+                     "evaluations in %.2f s" % (evals, dt)}
+    if total_chain_grads:
+        out["projected_run_s"] = total_chain_grads / v
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _rank_env()
     if rank != 0:
         return 0
     from paper_2601_16696_gb300 import workloads
-    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(_cpu_baseline(pr))
+    probs = workloads.batch64(n_steps=BATCH["n_steps"])
+    vals = [_batch_oracle(probs) for _ in range(args.warmup + args.steps)]
     timed = vals[args.warmup:]
     v = statistics.mean(r["value"] for r in timed)
-    ms = statistics.mean(1e3 * pr.M * 500 / r["value"] for r in timed)
+    ms = statistics.mean(1e3 * r["seconds"] for r in timed)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
-                       "switch": "after %d unadjusted steps (first full window)" % WORKLOAD["switch_at"],
-                       "parallelism": "host cores (the oracle)"},
+            "config": _batch_config(probs, {"parallelism": "host cores (the oracle)"}),
             "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v,
                                                                                     "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -277,9 +344,8 @@ def _forms(flush, stream, mhz, seed0):
     """The other forms of the path, measured in the same run and reported
     beside the headline: the logistic regression (d = 101 with intercept,
     n = 10^4 rows, M = 8192) with the BF16 tensor-core contraction in the
-    unadjusted phase beside the all-FP32 form; the batch of 64 uneven diagonal
-    Gaussians plus one d = 10^4, M = 16384 problem in one persistent launch; the
-    rotated ill-conditioned Gaussian (d = 100, M = 4096, dense precision).
+    unadjusted phase beside the all-FP32 form; the rotated ill-conditioned
+    Gaussian (d = 100, M = 4096, dense precision).
     Each: chain-gradient evaluations per second of a whole run, wall time to
     b^2 < 0.01, and the dominant kernel against its roofline.  Also the cost of
     an unadjusted iteration with the full-rank bias proxy (K = 20, 100)."""
@@ -304,13 +370,18 @@ def _forms(flush, stream, mhz, seed0):
     out = {}
     # ---- logistic regression
     pr = workloads.logreg(with_truth=True)
+    truth = "Laplace approximation of the posterior (FP64)"
+    ref = workloads.logreg_reference_moments()
+    if ref is not None:
+        pr.Ex2, pr.Varx2 = ref
+        truth = ("importance sampling from the Laplace Gaussian, FP64 "
+                 "(tests/golden/logreg_d101_n10000_moments.txt)")
     tg = laps.Target.from_problem(pr)
     x0 = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
     n = pr.X.shape[0]
     flops = 4.0 * pr.M * n * pr.d  # Z = W X^T and G = R X per gradient of the ensemble
     lr = {"workload": "logreg_d%d_n%d_M%d_%dsteps" % (pr.d, n, pr.M, pr.n_steps),
-          "b2": "b2_max", "truth": "Laplace approximation of the posterior (FP64)",
-          "switch": "paper rule (max delta < 0.01)"}
+          "b2": "b2_max", "truth": truth, "switch": "paper rule (max delta < 0.01)"}
     kernels = {0: "logreg_grad_f32_kernel<128>", 1: "logreg_grad_mma_kernel<128>",
                2: "logreg_grad_x3_kernel<128>"}
     for name, prec in (("mixed", 1), ("fp32", 0), ("bf16x3", 2)):
@@ -319,8 +390,9 @@ def _forms(flush, stream, mhz, seed0):
         reps = 10
         gms = timed_ms(lambda: [tg.logp_grad(x0, precision=prec) for _ in range(reps)]) / reps
         tg.check()
-        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, precision=prec, stop_b2=0.01,
-                         stop_b2_max=1)
+        # the whole 2000-step run (no early stop); the time to b^2_max < 0.01 is
+        # the device time from laps_init to the first iteration below it
+        s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, precision=prec, stop_b2_max=1)
         s.set_truth(pr.Ex2, pr.Varx2)
         s.init(x0, seed=seed0)
         s.step(3)  # warm-up of the launch sequence
@@ -333,6 +405,7 @@ def _forms(flush, stream, mhz, seed0):
             "value": pr.M * st["grads"] / (run_ms * 1e-3), "unit": UNIT,
             "run_ms": run_ms, "grads_per_chain": st["grads"], "t": st["t"], "phase": st["phase"],
             "time_to_b2_ms": st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None,
+            "grads_to_b2": st["b2_first_grads"] if st["b2_first_t"] >= 0 else None,
             "b2_max_final": st["b2_max"],
             "roofline": {"bound": "alu" if prec == 0 else "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -363,37 +436,6 @@ def _forms(flush, stream, mhz, seed0):
                      "b2_max_final": st["b2_max"]}
     tg.check()
     out["logreg_adjusted"] = adj
-    # ---- the batch
-    probs = workloads.batch64()
-    coords = sum(p.d * p.M for p in probs)
-    b = laps.Batch(probs, use_x0=False, n_total_steps=2000)
-    for k, p in enumerate(probs):
-        b.set_truth(k, p.Ex2, p.Varx2)
-    b.init(seed=seed0)
-    b.tune()
-    b.step(2)
-    it_ms = timed_ms(lambda: b.step(5)) / 5  # unadjusted iterations of every problem
-    b.init(seed=seed0 + 1)
-    run_ms = timed_ms(lambda: b.run(iters_per_launch=64))
-    sts = [b.stats(k) for k in range(len(probs))]
-    grads = sum(p.M * s["grads"] for p, s in zip(probs, sts))
-    firsts = [s["b2_first_ns"] / 1e6 for s in sts if s["b2_first_t"] >= 0]
-    achieved = coords * 16 / (it_ms * 1e-3) / 1e9
-    out["batch"] = {
-        "workload": "batch64: 64 Gaussians d in [10, 2000], M in {512..4096}, "
-                    "+ d=10000 M=16384; 2000 steps, paper switch rule",
-        "problems": len(probs), "coordinates": coords,
-        "value": grads / (run_ms * 1e-3), "unit": UNIT, "run_ms": run_ms,
-        "time_to_b2_ms": {"b2": "b2_avg", "reached": len(firsts), "of": len(probs),
-                          "max": max(firsts) if firsts else None,
-                          "median": statistics.median(firsts) if firsts else None},
-        "shape": b.shape(),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "batch_kernel<%d>" % b.shape()["coords_per_lane"],
-                     "basis": "16 B per coordinate-step (y, u read and written), %.3f ms per "
-                              "unadjusted iteration of the whole batch" % it_ms},
-    }
     # ---- the rotated ill-conditioned Gaussian (dense precision, streamed path)
     pr = workloads.icg()
     tg = laps.Target.from_problem(pr)
@@ -461,8 +503,12 @@ def ncu_case_form(which: str):
                          precision=1 if which == "logreg" else 2)
         s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)
         s.step(3)
-    elif which == "batch":
-        probs = [p for p in workloads.batch64() if p.d < 10000][:32]
+    elif which in ("batch", "batch_big"):
+        if which == "batch":
+            probs = [p for p in workloads.batch64() if p.d < 10000][:32]
+        else:  # the batch's d = 10^4 problem on 4096 of its chains (330 MB of state)
+            probs = [p for p in workloads.batch64() if p.d == 10000]
+            probs[0].M = 4096
         b = laps.Batch(probs, use_x0=False, n_total_steps=2000)
         b.init(seed=0)
         b.step(5)
@@ -551,21 +597,108 @@ def ncu_case(adjusted: bool = False):
     return 0
 
 
+def _resident_form(stream, seed0, peak, runs=5):
+    """The register-resident form on the banana target (d = 100, M = 4096, 5000
+    steps, switch forced at the first full window): whole-run throughput, time
+    to b^2_max < 0.01, the kernel against its ALU roofline, and the same run
+    end to end through the context API with host buffers."""
+    import torch
+    from paper_2601_16696_gb300 import laps, workloads
+    pr = workloads.banana(d=RESIDENT["d"], M=RESIDENT["M"], n_steps=RESIDENT["n_steps"])
+    tg = laps.Target.from_problem(pr)
+    cfg = dict(n_total_steps=pr.n_steps, force_switch_at=RESIDENT["switch_at"])
+    s = laps.Sampler(tg, pr.M, **cfg)
+    s.set_truth(pr.Ex2, pr.Varx2)
+    x0_dev = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
+    x0_host = torch.tensor(pr.x0, dtype=torch.float32).pin_memory()
+    out_host = torch.empty(pr.M, pr.d, dtype=torch.float32).pin_memory()
+    x0_e2e = torch.empty_like(x0_dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def timed(fn, n, sd0):
+        ts, b2 = [], []
+        for k in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(sd0 + k)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            st = s.stats()
+            b2.append(st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else None)
+        return ts, b2
+
+    def one(sd):
+        s.init(x0_dev, seed=sd)
+        s.run()
+
+    for k in range(3):
+        one(seed0 + k)
+    ts, b2 = timed(one, runs, seed0 + 10)
+    st = s.stats()
+    grads = st["grads"]
+    tr = s.trace()
+    n_unadj = sum(1 for r in tr[1:] if r["phase"] == 0 or r["t"] == st["t_switch"])
+    n_adj_grads = grads - 1 - n_unadj
+    ms = statistics.mean(ts)
+    info = s.launch_info()
+    kern = "laps_resident_kernel<banana,%d,%d>" % (info["lanes_per_chain"], info["coords_per_lane"])
+    ops = pr.M * pr.d * (n_unadj * ALU_OPS_LF + n_adj_grads * ALU_OPS_MN2_PER_GRAD)
+
+    def e2e_run(sd):
+        x0_e2e.copy_(x0_host, non_blocking=True)
+        s.init(x0_e2e, seed=sd)
+        s.run()
+        s.sample(out=x0_e2e)
+        out_host.copy_(x0_e2e, non_blocking=True)
+
+    te, _ = timed(e2e_run, runs, seed0 + 20)
+    # the kernel alone: events around laps_run (the initialisation is its own launch)
+    k_ms = []
+    for k in range(runs):
+        s.init(x0_dev, seed=seed0 + 30 + k)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.run()
+        b.record(stream)
+        b.synchronize()
+        k_ms.append(a.elapsed_time(b))
+    kms = statistics.mean(k_ms)
+    achieved = ops / (kms * 1e-3) / 1e9
+    hits = [v for v in b2 if v is not None]
+    return {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
+            "switch": "after %d unadjusted steps (first full window)" % RESIDENT["switch_at"],
+            "value": pr.M * grads / (ms * 1e-3), "unit": UNIT, "run_ms": ms, "runs": runs,
+            "grads_per_chain": grads, "launch": info,
+            "time_to_b2_ms": {"b2": "b2_max", "mean": statistics.mean(hits) if hits else None,
+                              "reached": len(hits), "of": runs},
+            "e2e": {"value": pr.M * grads / (statistics.mean(te) * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4},
+            "l2": "flushed (256 MB write) between runs",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                         "frac": achieved / peak, "traffic": _recorded_traffic(kern), "kernel": kern,
+                         "kernel_ms": kms, "alu_ops": ops}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="laps", choices=["laps", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="runs timed end to end (default: a quarter of --steps, at least 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the logistic-regression and batch forms")
+                    help="skip the other forms (resident, logistic regression, ...)")
     ap.add_argument("--ncu-case", action="store_true",
-                    help="no timing: the workload's launch shape, one launch of 200 unadjusted "
-                         "iterations after two others (the case profiled under ncu)")
+                    help="no timing: the resident workload's launch shape, one launch of 200 "
+                         "unadjusted iterations after two others (the case profiled under ncu)")
     ap.add_argument("--ncu-case-adjusted", action="store_true",
                     help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
-    ap.add_argument("--ncu-case-form", choices=["logreg", "logreg_x3", "batch", "dense"],
+    ap.add_argument("--ncu-case-form", choices=["logreg", "logreg_x3", "batch", "batch_big", "dense"],
                     help="no timing: a small case of another kernel (for ncu)")
     ap.add_argument("--ablations", action="store_true",
                     help="no contract line: the paper's ablations (MAMS only, fixed step, "
@@ -588,46 +721,55 @@ def main():
     torch.cuda.set_device(local)
     from paper_2601_16696_gb300 import build, laps, workloads
     build.build()
-
-    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
-    tg = laps.Target.from_problem(pr)
-    cfg = dict(n_total_steps=pr.n_steps, force_switch_at=WORKLOAD["switch_at"])
-    sampler = laps.Sampler(tg, pr.M, **cfg)
-    sampler.set_truth(pr.Ex2, pr.Varx2)
-    stopper = laps.Sampler(tg, pr.M, stop_b2=0.01, stop_b2_max=1, **cfg)
-    stopper.set_truth(pr.Ex2, pr.Varx2)
-    x0_dev = torch.tensor(pr.x0, dtype=torch.float32, device="cuda")
-    x0_host = torch.tensor(pr.x0, dtype=torch.float32).pin_memory()
-    out_host = torch.empty(pr.M, pr.d, dtype=torch.float32).pin_memory()
-    x0_e2e = torch.empty_like(x0_dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
     seed_base = 1000 * rank
+    K_ipl = BATCH["iters_per_launch"]
 
-    def one_run(s, seed):
-        s.init(x0_dev, seed=seed)
-        s.run()
+    # ---- the batch: initial positions in one device buffer (one H2D copy for e2e)
+    probs = workloads.batch64(n_steps=BATCH["n_steps"])
+    sizes = [p.M * p.d for p in probs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    total = int(offs[-1])
+    x0_host = torch.empty(total, dtype=torch.float32).pin_memory()
+    for p, o in zip(probs, offs):
+        x0_host[int(o):int(o) + p.M * p.d].copy_(torch.from_numpy(p.x0.astype(np.float32).ravel()))
+    x0_dev = x0_host.cuda()
+    out_dev = torch.empty(total, dtype=torch.float32, device="cuda")
+    out_host = torch.empty(total, dtype=torch.float32).pin_memory()
+    views = [dataclasses.replace(p, x0=x0_dev[int(o):int(o) + p.M * p.d].view(p.M, p.d))
+             for p, o in zip(probs, offs)]
+    outs = [out_dev[int(o):int(o) + p.M * p.d].view(p.M, p.d) for p, o in zip(probs, offs)]
+    b = laps.Batch(views, n_total_steps=BATCH["n_steps"], force_switch_at=BATCH["switch_at"])
+    for k, p in enumerate(probs):
+        b.set_truth(k, p.Ex2, p.Varx2)
+    b.init(seed=seed_base)
+    b.tune()
+    n = len(probs)
 
-    def timed(fn, n, seed0):
-        ts = []
+    def one_run(sd):
+        b.init(seed=sd)
+        b.run(iters_per_launch=K_ipl)
+
+    def e2e_run(sd):
+        x0_dev.copy_(x0_host, non_blocking=True)
+        b.init(seed=sd)
+        b.run(iters_per_launch=K_ipl)
         for k in range(n):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn(seed0 + k)
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        return ts
+            b.sample(k, out=outs[k])
+        out_host.copy_(out_dev, non_blocking=True)
 
-    # ---- warm-up
-    for k in range(args.warmup):
-        one_run(sampler, seed_base + k)
-        one_run(stopper, seed_base + k)
-    torch.cuda.synchronize()
-    st = sampler.stats()
-    grads = st["grads"]
+    def timed(fn, steps, sd0):
+        ts, b2 = [], []
+        for k in range(steps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(sd0 + k)
+            e.record(stream)
+            e.synchronize()
+            ts.append(a.elapsed_time(e))
+            sts = [b.stats(q) for q in range(n)]
+            b2.append(max(st["b2_first_ns"] / 1e6 if st["b2_first_t"] >= 0 else math.inf for st in sts))
+        return ts, b2, sts
 
     def barrier():
         if world > 1:
@@ -635,89 +777,110 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- warm-up
+    for k in range(args.warmup):
+        one_run(seed_base + k)
+    torch.cuda.synchronize()
+
     # ---- device-resident timing (the headline value)
     barrier()
     with Clocks(local) as clk:
-        ts = timed(lambda sd: one_run(sampler, sd), args.steps, seed_base + 100)
+        ts, b2, sts = timed(one_run, args.steps, seed_base + 100)
     barrier()
-    st = sampler.stats()
-    assert st["done"] and st["grads"] == grads, st
+    assert all(st["done"] for st in sts), "a problem did not finish"
+    chain_grads = sum(p.M * st["grads"] for p, st in zip(probs, sts))
     ms = _max_over_ranks(statistics.mean(ts))
-    value = world * pr.M * grads / (ms * 1e-3)
-
-    # ---- the kernel's own duration and its ALU roofline
-    info = sampler.launch_info()
-    tr = sampler.trace()
-    n_unadj = sum(1 for r in tr[1:] if r["phase"] == 0)
-    n_adj_grads = grads - 1 - n_unadj
-    k_ms = []
-    for k in range(args.steps):
-        sampler.init(x0_dev, seed=seed_base + 200 + k)
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sampler.run()
-        b.record(stream)
-        b.synchronize()
-        k_ms.append(a.elapsed_time(b))
-    kms = statistics.mean(k_ms)
-    coord = pr.M * pr.d
-    ops = coord * (n_unadj * ALU_OPS_LF + n_adj_grads * ALU_OPS_MN2_PER_GRAD)
+    value = world * chain_grads / (ms * 1e-3)
     clocks = clk.summary()
+
+    # ---- end to end through the batch entry points with host buffers
+    n_e2e = args.e2e_steps or max(2, args.steps // 4)
+    barrier()
+    te, _, _ = timed(e2e_run, n_e2e, seed_base + 200)
+    barrier()
+    e2e_ms = _max_over_ranks(statistics.mean(te))
+    e2e = {"value": world * chain_grads / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4,
+           "ms_per_step": e2e_ms, "steps": n_e2e}
+
+    # ---- the kernel's own duration: CUDA events around every launch of one run
+    b.init(seed=seed_base + 300)
+    kev = []
+    iters_max = BATCH["n_steps"] + 1
+    for r in range(iters_max // K_ipl + 2):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(K_ipl)
+        e.record(stream)
+        kev.append((a, e))
+    torch.cuda.synchronize()
+    launch_ms = [a.elapsed_time(e) for a, e in kev]
+    ksts = [b.stats(q) for q in range(n)]
+    live = [x for x in launch_ms if x > 0.05]  # launches after every problem finished return at once
+    kms = sum(live)
+    ops, hbm = 0.0, 0.0
+    n_unadj = {}
+    for k, (p, st) in enumerate(zip(probs, ksts)):
+        tr = b.trace(k)
+        nu = sum(1 for r in tr[1:] if r["phase"] == 0 or r["t"] == st["t_switch"])
+        npr = len(tr) - 1 - nu
+        n_unadj[k] = nu
+        # a proposal: the full velocity refresh (an O map's noise) and N steps
+        per_prop = OPS_O + 15 * BATCH_OPS_STEP[st["integrator"]] if st["integrator"] else 0.0
+        ops += p.M * p.d * (nu * BATCH_OPS_LF + npr * per_prop)
+        hbm += p.M * p.d * 16.0 * (nu + npr)  # y, u read and written once per iteration
     mhz = clocks["sm_mhz"] or 1455.0
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = nsm * 128 * mhz * 1e6 / 1e9  # FP32-pipe lane issue rate, Gop/s
     achieved = ops / (kms * 1e-3) / 1e9
-    traffic = _recorded_traffic("laps_resident_kernel<banana,%d,%d>"
-                                % (info["lanes_per_chain"], info["coords_per_lane"]))
+    pk = _peaks()
+    sh = b.shape()
+    kern = "batch_kernel<%d>" % sh["coords_per_lane"]
+    rec = _recorded(kern, "batch_counters.txt", BATCH_SRC)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "laps_resident_kernel<banana,%d,%d>" % (info["lanes_per_chain"],
-                                                                   info["coords_per_lane"]),
-                "kernel_ms": kms,
-                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (measured median)" % (nsm, mhz)}
-
-    # ---- wall time to b^2_max < 0.01
-    t2 = timed(lambda sd: one_run(stopper, sd), args.steps, seed_base + 300)
-    s2 = stopper.stats()
-    time_to_b2 = {"ms": statistics.mean(t2), "b2": "b2_max", "threshold": 0.01,
-                  "reached": s2["b2_max"] < 0.01, "t": s2["t"], "grads_per_chain": s2["grads"],
-                  "phase_at_stop": s2["phase"]}
-
-    # ---- end to end through the public API with host buffers
-    def e2e_run(seed):
-        x0_e2e.copy_(x0_host, non_blocking=True)
-        sampler.init(x0_e2e, seed=seed)
-        sampler.run()
-        sampler.sample(out=x0_e2e)
-        out_host.copy_(x0_e2e, non_blocking=True)
-
-    te = timed(e2e_run, args.steps, seed_base + 400)
-    e2e_ms = _max_over_ranks(statistics.mean(te))
-    e2e = {"value": world * pr.M * grads / (e2e_ms * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4,
-           "ms_per_step": e2e_ms}
+                "frac": achieved / peak, "traffic": None, "kernel": kern, "kernel_ms": kms,
+                "launches": len(live),
+                "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (measured median)" % (nsm, mhz),
+                "hbm": {"achieved_gbs": hbm / (kms * 1e-3) / 1e9, "peak_gbs": pk["hbm_gbs"],
+                        "frac": hbm / (kms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                        "basis": "16 B per coordinate and iteration (y, u read and written)"}}
+    if rec:
+        # [DRAM bytes per coordinate-iteration, warp instructions per coordinate-iteration]
+        # of one ncu capture of the small case, scaled by the coordinate-iterations of a launch
+        per_launch_ci = sum(p.M * p.d * (n_unadj[k] + (len(b.trace(k)) - 1 - n_unadj[k]))
+                            for k, p in enumerate(probs)) / len(live)
+        roofline["traffic"] = rec[0] * per_launch_ci
+        inst = rec[1] * sum(p.M * p.d * n_unadj[k] for k, p in enumerate(probs))
+        roofline["issue"] = {"warp_inst_per_coord_step": rec[1],
+                             "frac": inst / (kms * 1e-3) / (nsm * 4 * mhz * 1e6),
+                             "basis": "ncu smsp__inst_executed of the unadjusted small case; peak "
+                                      "%d SMs x 4 schedulers x 1 warp instruction per clock" % nsm}
 
     if rank == 0:
+        reached = [v for v in b2 if v < math.inf]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
-                       "switch": "after %d unadjusted steps (first full window)"
-                                 % WORKLOAD["switch_at"],
-                       "grads_per_chain": grads, "l2": "flushed (256 MB write) between runs",
-                       "launch": info, "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "time_to_b2": time_to_b2, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            "config": _batch_config(probs, {
+                "chain_grads_per_run": chain_grads, "shape": sh, "iters_per_launch": K_ipl,
+                "integrators": sorted({("MN4" if st["integrator"] == 2 else "MN2") for st in sts}),
+                "parallelism": "replicas" if world > 1 else "1 GPU"}),
+            "time_to_b2": {"ms": statistics.mean(reached) if reached else None, "b2": "b2_avg",
+                           "threshold": 0.01, "over": "every problem", "runs_reached": len(reached),
+                           "of": len(b2)},
+            "roofline": roofline, "e2e": e2e,
+            "gpu_launches": args.steps * (2 + BATCH["n_steps"] // K_ipl + 2),
+            "clocks": clocks,
         }
         if not args.no_forms:
-            line["forms"] = _forms(flush, stream, mhz, seed_base + 500)
+            forms = {"resident": _resident_form(stream, seed_base + 400, peak)}
+            forms.update(_forms(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"), stream, mhz,
+                                seed_base + 500))
+            line["forms"] = forms
             line["measured_peaks"] = _probe_peaks(stream)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = _cpu_baseline(pr, single_thread=True,
-                                                 grads_to_b2=time_to_b2.get("grads_per_chain"))
+            line["cpu_baseline"] = _batch_oracle(probs, total_chain_grads=chain_grads)
             if not args.no_forms:
                 line["cpu_baseline"]["other_workloads"] = _oracle_rates()
         print(json.dumps(line))

@@ -506,8 +506,11 @@ class Batch:
         _check(lib().laps_batch_get_trace(self._h, k, rows, n.value, C.byref(n)))
         return [_as_dict(rows[i]) for i in range(n.value)]
 
-    def sample(self, k: int, stream=None) -> torch.Tensor:
+    def sample(self, k: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         d, M = self.dims[k]
-        out = torch.empty(M, d, dtype=torch.float32, device="cuda")
+        if out is None:
+            out = torch.empty(M, d, dtype=torch.float32, device="cuda")
+        elif out.numel() != M * d:
+            raise ValueError("out must hold %d x %d values" % (M, d))
         _check(lib().laps_batch_sample(self._h, k, _ptr(out), _stream(stream)))
         return out

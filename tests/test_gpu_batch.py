@@ -122,6 +122,25 @@ def test_batch_graph_replay_equals_steps(L):
         np.testing.assert_array_equal(np.asarray(a), np.asarray(c))
 
 
+def test_batch_d10000_in_the_tuned_shape(L, ora):
+    """The batch's d = 10^4 problem in the shape the autotuner picks for the
+    whole batch (20 coordinates per lane, so one chain spans a 16-warp group),
+    beside a small problem: first steps at a fixed step size within 1e-5."""
+    probs = [W.gauss_diag(d=10000, M=256, n_steps=50, x0_scale=1.0, var_lo=1e-2, var_hi=1e2, seed=999),
+             W.gauss_diag(d=37, M=1000, n_steps=50, x0_scale=1.0, seed=5)]
+    b = L.Batch(probs, n_total_steps=50, fixed_eps=0.02)
+    b.set_shape(20, 0, 128)
+    assert b.shape()["coords_per_lane"] == 20 and b.shape()["threads"] == 512
+    b.init(seed=13)
+    refs = [_ora(ora, pr, 13, k, fixed_eps=0.02) for k, pr in enumerate(probs)]
+    for step in range(5):
+        b.step(1)
+        for k, r in enumerate(refs):
+            r.iterate(1)
+            rel = _rel(b.sample(k).double().cpu().numpy(), r.x())
+            assert rel <= 1e-5, (k, step + 1, rel)
+
+
 def test_batch_autotuner_keeps_parity(L, ora):
     probs = _probs(SPEC, 40)
     b = L.Batch(probs, n_total_steps=40, fixed_eps=0.05)

@@ -97,13 +97,17 @@ def test_dense_first_ten_steps_adaptive(L, ora, streamed):
     s = _gpu(L, pr, seed=3, dense_streamed=streamed)
     r = _ora(ora, pr, seed=3)
     r32 = _ora(ora, pr, seed=3, round_state_f32=1)
+    rows = []
     for k in range(10):
         s.step(1)
         r.iterate(1)
         r32.iterate(1)
         bar = max(1e-5, 3.0 * _rel(r32.x(), r.x()))
         rel = _rel(s.sample().double().cpu().numpy(), r.x())
+        rows.append("%d: %.1e / %.1e" % (k + 1, rel, bar))
         assert rel <= bar, (k + 1, rel, bar)
+    print("icg (%s) adaptive first steps, error / bar: %s"
+          % ("streamed" if streamed else "resident", ", ".join(rows)))
     assert s.trace()[1]["eps_used"] == pytest.approx(r.trace[1]["eps_used"], rel=1e-6)
 
 
@@ -127,31 +131,52 @@ def test_dense_final_b2_within_10_percent(L, ora, streamed):
     assert abs(bg - bo) <= 0.10 * bo, (bg, bo)
 
 
+_SWITCHED_SEEDS = (0, 1, 2, 3, 4)
+_switched_oracle = {}
+
+
+def _switched_oracle_runs(ora, pr, cfg):
+    """The oracle's switched runs, seeds 0..4 (computed once for both paths)."""
+    if not _switched_oracle:
+        for sd in _SWITCHED_SEEDS:
+            r = _ora(ora, pr, seed=sd, **cfg)
+            r.run()
+            _switched_oracle[sd] = (r.t, r.phase, r.t_switch, r.trace)
+    return _switched_oracle
+
+
 @pytest.mark.parametrize("streamed", PATHS)
 def test_dense_switched_run(L, ora, streamed):
     """Switch forced at step 400: the diagonal preconditioner cannot undo the
-    rotation, so MAMS is still removing bias at the end and its b^2 depends on
-    the path (oracle, 5 seeds: b^2_avg tail mean 0.0044-0.0062).  The step
-    size the bisection freezes at (0.239-0.245 over those seeds; it is set at
-    the first proposal within 0.03 of the target acceptance, so it moves in
-    steps of a few percent between paths) and the acceptance (0.72-0.74)
-    depend on it much less: they are held to 6% and 0.06, b^2_avg to twice the
-    seed spread."""
+    rotation, so MAMS is still removing bias at the end and one run's b^2
+    depends on its path (oracle seed spread of the b^2_avg tail mean 17%,
+    0.0044-0.0062).  The 10% bar on b^2 is therefore applied to means over
+    five seeds of the b^2_avg tail means.  The step size the bisection freezes at (0.239-0.245 over the seeds;
+    set at the first proposal within 0.03 of the target acceptance, so it
+    moves in steps of a few percent between paths) and the acceptance
+    (0.72-0.74) are held to 6% and 0.06 on seed 0."""
     pr = W.icg(M=1024, n_steps=2000)
     cfg = {"force_switch_at": 400}
-    s = _gpu(L, pr, seed=0, dense_streamed=streamed, **cfg)
-    s.run()
-    st = s.stats()
-    r = _ora(ora, pr, seed=0, **cfg)
-    r.run()
-    assert st["t"] == r.t and st["phase"] == r.phase == 1 and st["t_switch"] == r.t_switch == 400
-    tg = s.trace()
-    assert tg[-1]["eps"] == pytest.approx(r.trace[-1]["eps"], rel=0.06)
-    ag = np.mean([x["acc"] for x in tg[-20:]])
-    ao = np.mean([x["acc"] for x in r.trace[-20:]])
-    assert abs(ag - ao) <= 0.06, (ag, ao)
-    bg, bo = _tail(tg, "b2_avg", 1), _tail(r.trace, "b2_avg", 1)
-    assert abs(bg - bo) <= 0.35 * bo, (bg, bo)
+    ref = _switched_oracle_runs(ora, pr, cfg)
+    bgs, bos = [], []
+    for sd in _SWITCHED_SEEDS:
+        s = _gpu(L, pr, seed=sd, dense_streamed=streamed, **cfg)
+        s.run()
+        st = s.stats()
+        rt, rphase, rsw, rtrace = ref[sd]
+        assert st["t"] == rt and st["phase"] == rphase == 1 and st["t_switch"] == rsw == 400
+        tg = s.trace()
+        if sd == 0:
+            assert tg[-1]["eps"] == pytest.approx(rtrace[-1]["eps"], rel=0.06)
+            ag = np.mean([x["acc"] for x in tg[-20:]])
+            ao = np.mean([x["acc"] for x in rtrace[-20:]])
+            assert abs(ag - ao) <= 0.06, (ag, ao)
+        bgs.append(_tail(tg, "b2_avg", 1))
+        bos.append(_tail(rtrace, "b2_avg", 1))
+    bg, bo = float(np.mean(bgs)), float(np.mean(bos))
+    print("dense switched run (%s): b^2_avg tail, 5-seed mean: GPU %.4g, oracle %.4g"
+          % ("streamed" if streamed else "resident", bg, bo))
+    assert abs(bg - bo) <= 0.10 * bo, (bgs, bos)
 
 
 @pytest.mark.parametrize("streamed", PATHS)

@@ -112,6 +112,7 @@ def test_logreg_first_ten_steps_adaptive(L, ora):
     s = _gpu(L, pr, seed=3)
     r = _ora(ora, pr, seed=3)
     r32 = _ora(ora, pr, seed=3, round_state_f32=1)
+    rows = []
     for k in range(10):
         s.step(1)
         r.iterate(1)
@@ -119,7 +120,9 @@ def test_logreg_first_ten_steps_adaptive(L, ora):
         xr = r.x()
         bar = max(1e-5, 3.0 * _rel(r32.x(), xr))
         rel = _rel(s.sample().double().cpu().numpy(), xr)
+        rows.append("%d: %.1e / %.1e" % (k + 1, rel, bar))
         assert rel <= bar, (k + 1, rel, bar)
+    print("logreg adaptive first steps, error / bar: %s" % ", ".join(rows))
 
 
 def test_logreg_adjusted_proposals_match(L, ora):
@@ -219,18 +222,27 @@ def test_mixed_first_steps_error_stated(L, ora):
     assert max(errs) < 1e-4, errs
 
 
-def test_mixed_whole_run_matches_fp32(L, ora):
+def test_mixed_whole_run_matches_oracle(L, ora):
+    """A whole mixed-precision run (BF16 tensor-core contraction while
+    unadjusted, FP32 once adjusted) against the FP64 oracle on the FP32 data:
+    the adjusted phase's Metropolis test targets the FP32 posterior, so the
+    final ensemble is held to the FP32 form's bar, b^2 of its second moments
+    against the oracle's final ensemble below 10/M (two independent ensembles
+    of the same posterior give ~2/M)."""
     pr = W.logreg(n_data=1000, M=512, n_steps=400)
     cfg = dict(force_switch_at=100)
     a = _gpu(L, pr, seed=0, precision=1, **cfg)
     a.run()
-    b = _gpu(L, pr, seed=0, precision=0, **cfg)
-    b.run()
-    sa, sb = a.stats(), b.stats()
-    assert sa["t"] == sb["t"] and sa["t_switch"] == sb["t_switch"] == 100
-    xa, xb = a.sample().double().cpu().numpy(), b.sample().double().cpu().numpy()
-    m2a, m2b, v2b = (xa ** 2).mean(0), (xb ** 2).mean(0), (xb ** 2).var(0)
-    assert float(np.mean((m2a - m2b) ** 2 / v2b)) < 10.0 / pr.M
+    r = _ora(ora, pr, seed=0, **cfg)
+    r.run()
+    sa = a.stats()
+    assert sa["t"] == r.t and sa["t_switch"] == r.t_switch == 100 and sa["integrator"] == r.integrator
+    xa, xr = a.sample().double().cpu().numpy(), r.x()
+    m2a, m2r, v2r = (xa ** 2).mean(0), (xr ** 2).mean(0), (xr ** 2).var(0)
+    b2 = float(np.mean((m2a - m2r) ** 2 / v2r))
+    print("mixed whole run: b^2 of the final second moments against the oracle's %.2e (bar %.2e)"
+          % (b2, 10.0 / pr.M))
+    assert b2 < 10.0 / pr.M, b2
     # the adjusted phase tests log p of one arithmetic: acceptance is sane from the first proposal
     rows = [r for r in a.trace() if r["phase"] == 1 and r["acc"] == r["acc"]]
     assert rows[0]["acc"] > 0.5, rows[0]

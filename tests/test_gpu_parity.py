@@ -148,6 +148,7 @@ def test_first_ten_steps_adaptive(L, ora, name):
     s = _gpu(L, pr, seed=3)
     r = _ora(ora, pr, seed=3)
     r32 = _ora(ora, pr, seed=3, round_state_f32=1)
+    rows = []
     for k in range(10):
         s.step(1)
         r.iterate(1)
@@ -155,7 +156,9 @@ def test_first_ten_steps_adaptive(L, ora, name):
         xr = r.x()
         bar = max(1e-5, 3.0 * _rel(r32.x(), xr))
         rel = _rel(s.sample().double().cpu().numpy(), xr)
+        rows.append("%d: %.1e / %.1e" % (k + 1, rel, bar))
         assert rel <= bar, (k + 1, rel, bar)
+    print("%s adaptive first steps, error / bar: %s" % (name, ", ".join(rows)))
     # step 1 uses eps0 and L0 only: it meets the plain bar
     tg = s.trace()
     assert tg[1]["eps_used"] == pytest.approx(r.trace[1]["eps_used"], rel=1e-6)
