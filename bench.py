@@ -682,6 +682,49 @@ def _resident_form(stream, seed0, peak, runs=5):
                          "kernel_ms": kms, "alu_ops": ops}}
 
 
+def _sharded_logreg(stream, world, rank, seed0, runs=2):
+    """The chain-sharded ensemble (laps_create_sharded) on the logistic
+    regression (d = 101, n = 10^4, M = 8192, mixed precision, 2000 steps): each
+    rank advances M / N chains and exchanges its column totals once per
+    iteration (an NCCL all-gather; a local copy on one rank).  Every rank calls
+    this; the value counts all ranks' chains over the slowest rank's time."""
+    import torch
+    from paper_2601_16696_gb300 import laps, workloads
+    pr = workloads.logreg()
+    tg = laps.Target.from_problem(pr)
+    m0, m1 = rank * pr.M // world, (rank + 1) * pr.M // world
+    fn = laps.nccl_allgather() if world > 1 else None
+    s = laps.Sampler(tg, m1 - m0, n_total_steps=pr.n_steps, precision=1,
+                     shard=(pr.M, m0, rank, world, fn))
+    x0 = torch.tensor(pr.x0[m0:m1], dtype=torch.float32, device="cuda")
+    one = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, precision=1) if world == 1 else None
+    x0_all = torch.tensor(pr.x0, dtype=torch.float32, device="cuda") if world == 1 else None
+
+    def timed(smp, x, sd):
+        smp.init(x, seed=sd)
+        smp.step(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        smp.init(x, seed=sd + 1)
+        smp.run()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    ts = [timed(s, x0, seed0 + 2 * k) for k in range(runs)]
+    ms = _max_over_ranks(min(ts))
+    st = s.stats()
+    out = {"workload": "logreg_d%d_n%d_M%d_%dsteps, mixed precision, %d rank(s) of %d chains"
+                       % (pr.d, pr.X.shape[0], pr.M, pr.n_steps, world, m1 - m0),
+           "value": pr.M * st["grads"] / (ms * 1e-3), "unit": UNIT, "run_ms": ms,
+           "grads_per_chain": st["grads"], "t": st["t"],
+           "exchange": "NCCL all-gather of 4 d_pad + 5 float-float pairs per rank and iteration"
+                       if world > 1 else "one rank: a local copy of its totals"}
+    if one is not None:
+        out["unsharded_run_ms"] = min(timed(one, x0_all, seed0 + 10 + 2 * k) for k in range(runs))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -856,6 +899,9 @@ def main():
                              "basis": "ncu smsp__inst_executed of the unadjusted small case; peak "
                                       "%d SMs x 4 schedulers x 1 warp instruction per clock" % nsm}
 
+    # every rank draws from the same seed: the ranks hold parts of one ensemble
+    sharded = None if args.no_forms else _sharded_logreg(stream, world, rank, 600)
+
     if rank == 0:
         reached = [v for v in b2 if v < math.inf]
         line = {
@@ -877,6 +923,7 @@ def main():
             forms = {"resident": _resident_form(stream, seed_base + 400, peak)}
             forms.update(_forms(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"), stream, mhz,
                                 seed_base + 500))
+            forms["logreg_sharded"] = sharded
             line["forms"] = forms
             line["measured_peaks"] = _probe_peaks(stream)
         if not args.no_cpu_baseline:

@@ -319,6 +319,37 @@ laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M, const laps
                              const float* x0, double x0_scale, uint64_t seed, float* x_out,
                              laps_stats* stats_out, void* stream);
 
+/* ---- a chain-sharded ensemble ------------------------------------------
+ * Chains are independent between the ensemble reductions (Sec. 2, Eq. "ECA";
+ * Alg. 1), so one ensemble of M_total chains can be split over ranks (one
+ * process per GPU): each rank advances its own chains m0 .. m0 + M_local - 1
+ * (their Philox counters carry the global chain index, so the union of the
+ * ranks' chains is the unsharded ensemble) and, once per Alg. 1 iteration,
+ * exchanges only its totals of the per-coordinate and per-chain sums the
+ * finalise needs (4 d_pad + 5 float-float pairs).  Every rank then adds the
+ * totals in rank order and runs the identical finalise, so every rank holds
+ * the same step size, L, window and phase machine.
+ * The exchange is the caller's: allgather(send, recv, bytes, stream, user)
+ * must gather `bytes` of device memory from every rank's `send` into `recv`
+ * [n_ranks][bytes], in rank order, stream-ordered on `stream` (e.g. an NCCL
+ * all-gather), and return 0; it is called on the host thread that enqueues the
+ * iteration, once per iteration (also for the initialisation).  With
+ * n_ranks = 1 it may be NULL (a local copy).  Served on the streamed path:
+ * LOGREG and USER targets, GAUSS_DENSE beyond d = 128 or with dense_streamed;
+ * other targets return LAPS_ERR_UNSUPPORTED.  With one rank the results equal
+ * laps_create's bit for bit. */
+typedef int (*laps_allgather_fn)(const void* send, void* recv, size_t bytes, void* stream,
+                                 void* user_data);
+typedef struct {
+    int64_t M_total;             /* chains of the whole ensemble */
+    int64_t m0;                  /* global index of this rank's first chain */
+    int rank, n_ranks;
+    laps_allgather_fn allgather;
+    void* user_data;             /* passed to allgather unchanged */
+} laps_shard;
+laps_status laps_create_sharded(const laps_target* tg, int64_t M_local, const laps_shard* shard,
+                                const laps_config* cfg, laps_ctx** out);
+
 /* Launch shape the context uses (for tests and the autotuner). */
 typedef struct {
     int chains_per_block, lanes_per_chain, coords_per_lane, threads, blocks;

@@ -262,6 +262,8 @@ void fill_params(const laps_ctx* c, int mode, const float* x0, float x0_scale, K
     P.smax = c->smax;
     P.bar_extra = g.barrier_extra_arrivals;
     P.dfull_K = g.dtilde_K;
+    P.m0 = (int)c->m0;
+    P.Mn = c->sharded ? (int)c->M_total : 0;
     P.phase_ns = c->phase_ns;
     P.yw = c->yw;
     P.uw = c->uw;
@@ -513,6 +515,46 @@ laps_status laps_create(const laps_target* tg, int64_t M, const laps_config* cfg
     cudaMemset(c->g, 0, Md * 4);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { laps_destroy(c); return cuda_fail(e, "laps_create"); }
+    *out = c;
+    return LAPS_OK;
+}
+
+laps_status laps_create_sharded(const laps_target* tg, int64_t M_local, const laps_shard* sh,
+                                const laps_config* cfg, laps_ctx** out) {
+    if (!tg || !sh || !cfg || !out) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (sh->n_ranks < 1 || sh->rank < 0 || sh->rank >= sh->n_ranks || sh->m0 < 0 || M_local < 2 ||
+        sh->m0 + M_local > sh->M_total || sh->M_total > (1LL << 30))
+        return fail(LAPS_ERR_INVALID_ARG, "shard: need 0 <= rank < n_ranks and 0 <= m0, m0 + M_local <= M_total");
+    if (sh->n_ranks > 1 && !sh->allgather)
+        return fail(LAPS_ERR_INVALID_ARG, "shard: more than one rank needs an allgather callback");
+    const bool streamed = streamed_kind(tg->kind) &&
+                          !(tg->kind == TGT_GAUSS_DENSE && tg->d_pad <= kDenseResidentMax && !cfg->dense_streamed);
+    if (!streamed)
+        return fail(LAPS_ERR_UNSUPPORTED, "a chain-sharded ensemble runs on the streamed path (LOGREG, USER, "
+                                          "GAUSS_DENSE beyond d = 128 or with dense_streamed)");
+    laps_ctx* c = nullptr;
+    laps_status st = laps_create(tg, M_local, cfg, &c);
+    if (st != LAPS_OK) return st;
+    c->sharded = true;
+    c->M_total = sh->M_total;
+    c->m0 = sh->m0;
+    c->rank = sh->rank;
+    c->n_ranks = sh->n_ranks;
+    c->shard_fn = sh->allgather;
+    c->shard_user = sh->user_data;
+    const size_t rows = rows_fb(c->d_pad);
+    auto alloc = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        c->allocs.push_back(*p);
+        return true;
+    };
+    if (!(alloc((void**)&c->shard_send, rows * sizeof(float2)) &&
+          alloc((void**)&c->shard_recv, (size_t)c->n_ranks * rows * sizeof(float2)) &&
+          alloc((void**)&c->shard_part, (size_t)c->n_ranks * rows * sizeof(float2)))) {
+        laps_destroy(c);
+        return fail(LAPS_ERR_OOM, "device allocation of the shard exchange buffers failed");
+    }
     *out = c;
     return LAPS_OK;
 }

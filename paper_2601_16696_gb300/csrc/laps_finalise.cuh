@@ -105,7 +105,7 @@ __device__ __forceinline__ void ens_slice(const KParams& P, const Hyper& H, ff* 
         }
     }
     __syncthreads();
-    const float iM = 1.0f / (float)P.M;
+    const float iM = 1.0f / (float)ens_chains(P);
     for (int k = tid; k < ns; k += blockDim.x) {
         const int i = i0 + k;
         const ff mean = ff_mulf(s_q[0 * P.smax + k], iM);
@@ -396,7 +396,7 @@ __device__ __forceinline__ void ens_gather(const KParams& P, Hyper& H, float* s_
                 }
             } else {
                 // Sec. 5.1: mean acceptance, bisection until |a - a*| <= tol
-                const float a = ff_f(tot[CS_ASUM]) / (float)P.M;
+                const float a = ff_f(tot[CS_ASUM]) / (float)ens_chains(P);
                 const float nbad = ff_f(tot[CS_NBAD]);
                 h.eps_used = h.eps;
                 h.adapting = h.adapting && (fabsf(a - h.a_target) > P.acc_tol);

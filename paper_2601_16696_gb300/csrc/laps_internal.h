@@ -69,6 +69,15 @@ struct laps_ctx {
     int nsplit_mma = 1, rps_mma = 64;
     int nsplit_x3 = 1, rps_x3 = 64;   // the three-term tensor-core form's data splits
     alignas(64) unsigned char tmW[128];  // CUtensorMap of Wb
+    // chain-sharded ensemble (laps_create_sharded): chains m0 .. m0 + M - 1 of M_total
+    bool sharded = false;
+    int64_t M_total = 0, m0 = 0;
+    int rank = 0, n_ranks = 1;
+    laps_allgather_fn shard_fn = nullptr;
+    void* shard_user = nullptr;
+    float2* shard_send = nullptr;   // [rows] this rank's column totals
+    float2* shard_recv = nullptr;   // [n_ranks][rows] every rank's, in rank order
+    float2* shard_part = nullptr;   // [rows][n_ranks] the same, in the columns layout the finalise reads
 };
 
 namespace laps {

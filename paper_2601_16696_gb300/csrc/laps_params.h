@@ -91,7 +91,13 @@ struct KParams {
     void* Wb;                 // mixed precision: [M_pad][2 d_pad] BF16 (hi | lo) copy of W
     int gauss_derived;        // batched diagonal Gaussians: only y, y^2 are summed per coordinate
     int dfull_K;              // > 0: full-rank D~ over this many Rademacher vectors (else diagonal)
+    // chain-sharded ensemble (streamed path): this context holds chains m0 .. m0 + M - 1 of an
+    // ensemble of Mn chains; the Philox counters carry the global index, the finalise divides
+    // by Mn.  m0 = 0, Mn = 0 (meaning M): the whole ensemble.
+    int m0, Mn;
 };
+// chains of the whole ensemble (the finalise's normalisation)
+__host__ __device__ inline int ens_chains(const KParams& P) { return P.Mn > 0 ? P.Mn : P.M; }
 
 // per-coordinate result slot of the full-rank bias proxy: sum_k (z_ki + c_ik)^2,
 // and the ensemble means E[y_i], E[g_i] it centres the next iteration on

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
     };
 
     for (int m = mb0 + warp; m < mb1; m += kSegWarps) {
+        const uint32_t mg = (uint32_t)(m + P.m0);  // the chain's index in the whole ensemble
         float y[CPL], u[CPL], g[CPL];
         ff lp = ff_make(0.0f), dl = ff_make(0.0f);
         if (op.init == 1) {
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
                 const int j = lane + 32 * k;
                 float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 if (j < P.nblk && P.x0 == nullptr)
-                    normals4(j, m, 0u, TAG_X0 | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+                    normals4(j, mg, 0u, TAG_X0 | (P.pid << 8), P.seed_lo, P.seed_hi, z);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int i = 4 * j + c;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
             n2 = group_sum<32>(n2);
 #pragma unroll
             for (int q = 0; q < CPL; ++q) u[q] = 0.0f;
-            o_update<32, CPL>(P, lane, true, m, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
+            o_update<32, CPL>(P, lane, true, mg, 0xFFFFFFFFu, TAG_O1, 0.0f, 1.0f, u);
             if (n2 > 0.0f) {
                 const float inv = 1.0f / sqrtf(n2);
 #pragma unroll
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
                     const int j = lane + 32 * k;
                     float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     if (j < P.nblk)
-                        normals4(j, m, (uint32_t)H.p, TAG_REFRESH | (P.pid << 8), P.seed_lo, P.seed_hi, z);
+                        normals4(j, mg, (uint32_t)H.p, TAG_REFRESH | (P.pid << 8), P.seed_lo, P.seed_hi, z);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const float v = (4 * j + c < P.d) ? z[c] : 0.0f;
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
                 for (int q = 0; q < CPL; ++q) u[q] *= inv;
             }
             if (op.bA != 0.0f) b_update<32, CPL>(op.bA * eps, inv_dm1, dm1, g, u, dl);
-            if (op.o2_step >= 0) o_update<32, CPL>(P, lane, true, m, t0 + op.o2_step, TAG_O2, c1, c2s, u);
-            if (op.o1_step >= 0) o_update<32, CPL>(P, lane, true, m, t0 + op.o1_step, TAG_O1, c1, c2s, u);
+            if (op.o2_step >= 0) o_update<32, CPL>(P, lane, true, mg, t0 + op.o2_step, TAG_O2, c1, c2s, u);
+            if (op.o1_step >= 0) o_update<32, CPL>(P, lane, true, mg, t0 + op.o1_step, TAG_O1, c1, c2s, u);
             if (op.bB != 0.0f) b_update<32, CPL>(op.bB * eps, inv_dm1, dm1, g, u, dl);
             if (op.a != 0.0f) {
                 const float ae = op.a * eps;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kSegThreads, CPL <= 4 ? 3 : 1) seg_kernel(cons
             float a_m = 0.0f;
             if (H.phase == 1) {
                 const uint4 r = philox4x32_10(
-                    make_uint4(0u, (uint32_t)m, (uint32_t)H.p, TAG_MH | (P.pid << 8)), P.seed_lo,
+                    make_uint4(0u, mg, (uint32_t)H.p, TAG_MH | (P.pid << 8)), P.seed_lo,
                     P.seed_hi);
                 const ff s = ff_add(dl, logf(u01(r.x)));
                 keep = !bad && (s.hi < 0.0f || (s.hi == 0.0f && s.lo < 0.0f));
@@ -369,6 +370,25 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const KParams P) {
         }
 }
 
+// Chain-sharded ensemble: this rank's totals of every column row (the block
+// columns added in the order and grouping the finalise's slice owners use, so
+// that one rank reproduces the unsharded sums bit for bit).  One warp per row.
+__global__ void rank_totals_kernel(const float2* __restrict__ part, int G, int rows, float2* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= rows) return;
+    ff s = lane_col_sum(part + (size_t)row * G, G, lane, 32);
+    s = group_sum_ff<32>(s);
+    if (lane == 0) out[row] = make_float2(s.hi, s.lo);
+}
+// every rank's totals [n][rows] (rank order) into the columns layout [rows][n]
+__global__ void shard_columns_kernel(const float2* __restrict__ recv, int n, int rows, float2* __restrict__ part) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * rows) return;
+    const int r = k / rows, row = k - r * rows;
+    part[(size_t)row * n + r] = recv[k];
+}
+
 // Sec. 4, once after the switch: y = x / sigma and g_y = sigma g_x of the accepted state
 __global__ void precondition_kernel(const KParams P) {
     const int64_t n = (int64_t)P.M * P.d_pad;
@@ -433,8 +453,33 @@ int nsplit_of(const laps_ctx* c, int form) {
 }
 
 laps_status launch_fin(laps_ctx* c, const KParams& P, cudaStream_t st) {
-    fin_kernel<<<c->fin_G, kFinThreads, std::max(c->fin_slice_smem, c->fin_gather_smem), st>>>(P);
+    if (!c->sharded) {
+        fin_kernel<<<c->fin_G, kFinThreads, std::max(c->fin_slice_smem, c->fin_gather_smem), st>>>(P);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "finalise kernel");
+    }
+    // the one exchange of a chain-sharded iteration (Eq. ECA's sums): this rank's
+    // column totals, gathered from every rank in rank order, then the finalise on
+    // the gathered columns (one per rank), identical on every rank
+    const int rows = (int)rows_fb(c->d_pad);
+    rank_totals_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(c->part, P.G, rows, c->shard_send);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rank totals kernel");
+    const size_t bytes = (size_t)rows * sizeof(float2);
+    if (c->shard_fn) {
+        const int r = c->shard_fn(c->shard_send, c->shard_recv, bytes, (void*)st, c->shard_user);
+        if (r != 0) return fail(LAPS_ERR_CUDA, "allgather callback returned " + std::to_string(r));
+    } else {
+        e = cudaMemcpyAsync(c->shard_recv, c->shard_send, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of the rank totals");
+    }
+    const int n = c->n_ranks;
+    shard_columns_kernel<<<(n * rows + 255) / 256, 256, 0, st>>>(c->shard_recv, n, rows, c->shard_part);
+    KParams Q = P;
+    Q.part = c->shard_part;
+    Q.G = n;
+    fin_kernel<<<c->fin_G, kFinThreads, std::max(c->fin_slice_smem, c->fin_gather_smem), st>>>(Q);
+    e = cudaGetLastError();
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "finalise kernel");
 }
 

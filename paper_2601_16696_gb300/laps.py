@@ -128,6 +128,7 @@ SIGNATURES = {
     "laps_target_logp_grad_prec": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int, _vp]),
     "laps_target_status": (C.c_int, [_vp]),
     "laps_create": (C.c_int, [_vp, C.c_int64, C.POINTER(Config), C.POINTER(_vp)]),
+    "laps_create_sharded": (C.c_int, [_vp, C.c_int64, C.c_void_p, C.POINTER(Config), C.POINTER(_vp)]),
     "laps_destroy": (None, [_vp]),
     "laps_init": (C.c_int, [_vp, _vp, C.c_double, C.c_uint64, _vp]),
     "laps_step": (C.c_int, [_vp, C.c_int, _vp]),
@@ -304,14 +305,69 @@ class Target:
             self._h = None
 
 
-class Sampler:
-    """One LAPS run of M chains on a Target (Algorithm 1 on the GPU)."""
+_ALLGATHER = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
-    def __init__(self, target: Target, M: int, config: Config | None = None, **cfg_kw):
+
+class ShardSpec(C.Structure):
+    _fields_ = [("M_total", C.c_int64), ("m0", C.c_int64), ("rank", C.c_int), ("n_ranks", C.c_int),
+                ("allgather", _ALLGATHER), ("user_data", C.c_void_p)]
+
+
+class _DeviceBytes:
+    """A device range seen by torch (no copy) through the CUDA array interface."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def device_bytes(ptr: int, nbytes: int) -> torch.Tensor:
+    return torch.as_tensor(_DeviceBytes(ptr, nbytes), device="cuda")
+
+
+def nccl_allgather(group=None):
+    """The exchange of a chain-sharded ensemble over torch.distributed (NCCL):
+    gathers every rank's totals in rank order on the sampler's stream."""
+    import torch.distributed as dist
+
+    def gather(send: int, recv: int, nbytes: int, stream: int):
+        with torch.cuda.stream(torch.cuda.ExternalStream(stream)):
+            dist.all_gather_into_tensor(device_bytes(recv, nbytes * dist.get_world_size(group)),
+                                        device_bytes(send, nbytes), group=group)
+    return gather
+
+
+class Sampler:
+    """One LAPS run of M chains on a Target (Algorithm 1 on the GPU).
+
+    shard: None, or (M_total, m0, rank, n_ranks, allgather) for a chain-sharded
+    ensemble (laps_create_sharded): this sampler holds chains m0 .. m0 + M - 1 of
+    M_total; allgather(send_ptr, recv_ptr, nbytes, stream_ptr) gathers every
+    rank's totals (device memory) in rank order on that stream, e.g.
+    nccl_allgather(); None with one rank."""
+
+    def __init__(self, target: Target, M: int, config: Config | None = None, shard=None, **cfg_kw):
         self.target, self.M, self.d = target, M, target.d
         self.config = config if config is not None else default_config(**cfg_kw)
         h = C.c_void_p()
-        _check(lib().laps_create(target.handle, M, C.byref(self.config), C.byref(h)))
+        if shard is None:
+            _check(lib().laps_create(target.handle, M, C.byref(self.config), C.byref(h)))
+        else:
+            M_total, m0, rank, n_ranks, fn = shard
+
+            def cb(send, recv, nbytes, stream, user):
+                try:
+                    fn(send, recv, nbytes, stream)
+                    return 0
+                except Exception:  # reported by the library as a failed callback
+                    import traceback
+                    traceback.print_exc()
+                    return 1
+            self._cb = _ALLGATHER(cb) if fn is not None else _ALLGATHER()
+            spec = ShardSpec(M_total, m0, rank, n_ranks, self._cb, None)
+            self._spec = spec
+            _check(lib().laps_create_sharded(target.handle, M, C.cast(C.pointer(spec), C.c_void_p),
+                                             C.byref(self.config), C.byref(h)))
         self._h = h
 
     def __del__(self):

@@ -44,13 +44,14 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_2601_16696_gb300 import laps
     prog = tmp_path / "sizes.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "laps.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d %d %d %d\\n",'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d %d %d %d\\n",'
                     'sizeof(laps_config), sizeof(laps_stats), sizeof(laps_trace_row),'
                     'sizeof(laps_target_desc), sizeof(laps_launch_info),'
                     'offsetof(laps_config, barrier_extra_arrivals),'
                     'offsetof(laps_stats, b2_first_ns), sizeof(laps_problem),'
                     'offsetof(laps_problem, x0_scale), sizeof(laps_batch_shape),'
                     'sizeof(laps_peaks), offsetof(laps_peaks, grid_barrier_us),'
+                    'sizeof(laps_shard), offsetof(laps_shard, user_data),'
                     '(int)LAPS_FP32, (int)LAPS_MIXED, (int)LAPS_BF16X3, (int)LAPS_MIXED_BF16X3);return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HDR), str(prog), "-o", str(exe)], check=True)
@@ -62,6 +63,7 @@ def test_struct_layouts_match_c(tmp_path):
             laps.Config.barrier_extra_arrivals.offset, laps.Stats.b2_first_ns.offset,
             C.sizeof(laps.Problem), laps.Problem.x0_scale.offset, C.sizeof(laps.BatchShape),
             C.sizeof(laps.Peaks), laps.Peaks.grid_barrier_us.offset,
+            C.sizeof(laps.ShardSpec), laps.ShardSpec.user_data.offset,
             laps.FP32, laps.MIXED, laps.BF16X3, laps.MIXED_BF16X3]
     assert got == want
 
