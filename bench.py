@@ -503,16 +503,22 @@ def ncu_case_form(which: str):
                          precision=1 if which == "logreg" else 2)
         s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)
         s.step(3)
-    elif which in ("batch", "batch_big"):
-        if which == "batch":
-            probs = [p for p in workloads.batch64() if p.d < 10000][:32]
-        else:  # the batch's d = 10^4 problem on 4096 of its chains (330 MB of state)
+    elif which in ("batch", "batch_big", "batch_adj", "batch_big_adj"):
+        if which.startswith("batch_big"):  # the batch's d = 10^4 problem on 4096 of its chains (330 MB)
             probs = [p for p in workloads.batch64() if p.d == 10000]
             probs[0].M = 4096
-        b = laps.Batch(probs, use_x0=False, n_total_steps=2000)
+        else:
+            probs = [p for p in workloads.batch64() if p.d < 10000][:32]
+        adj = which.endswith("_adj")
+        b = laps.Batch(probs, use_x0=False, n_total_steps=2000, **({"force_switch_at": 1} if adj else {}))
+        b.set_shape(20, 0, 128)  # the shape the autotuner picks for the whole batch
         b.init(seed=0)
-        b.step(5)
-        b.step(5)
+        if adj:
+            b.step(1)  # launch 2: the first unadjusted step and the switch
+            b.step(2)  # launch 3: two MAMS proposals of every problem
+        else:
+            b.step(5)  # launches 2 and 3: five unadjusted iterations each
+            b.step(5)
         info.update(coordinates=sum(p.d * p.M for p in probs), shape=b.shape())
     else:
         pr = workloads.icg()
@@ -668,6 +674,16 @@ def _resident_form(stream, seed0, peak, runs=5):
     kms = statistics.mean(k_ms)
     achieved = ops / (kms * 1e-3) / 1e9
     hits = [v for v in b2 if v is not None]
+    n_prop = sum(1 for r in tr[1:] if r["phase"] == 1 and r["t"] != st["t_switch"])
+    rec = _recorded(kern)  # [DRAM bytes per launch, warp instructions per coordinate: LF step, proposal]
+    issue = None
+    if rec and len(rec) >= 3:
+        inst = pr.M * pr.d * (n_unadj * rec[1] + n_prop * rec[2])
+        issue = {"frac": inst / (kms * 1e-3) / (peak * 1e9 / 32.0),
+                 "warp_inst_per_coord": {"lf_step": rec[1], "proposal": rec[2]},
+                 "basis": "ncu smsp__inst_executed of an unadjusted and an adjusted launch "
+                          "(profiles/resident_traffic.txt) over the kernel time, against SMs x 4 "
+                          "schedulers x 1 warp instruction per clock"}
     return {"workload": "%s_M%d_%dsteps" % (pr.name, pr.M, pr.n_steps),
             "switch": "after %d unadjusted steps (first full window)" % RESIDENT["switch_at"],
             "value": pr.M * grads / (ms * 1e-3), "unit": UNIT, "run_ms": ms, "runs": runs,
@@ -679,7 +695,7 @@ def _resident_form(stream, seed0, peak, runs=5):
             "l2": "flushed (256 MB write) between runs",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                          "frac": achieved / peak, "traffic": _recorded_traffic(kern), "kernel": kern,
-                         "kernel_ms": kms, "alu_ops": ops}}
+                         "kernel_ms": kms, "alu_ops": ops, "issue": issue}}
 
 
 def _sharded_logreg(stream, world, rank, seed0, runs=2):
@@ -741,7 +757,8 @@ def main():
                          "unadjusted iterations after two others (the case profiled under ncu)")
     ap.add_argument("--ncu-case-adjusted", action="store_true",
                     help="no timing: as --ncu-case, the third launch runs 10 MAMS proposals")
-    ap.add_argument("--ncu-case-form", choices=["logreg", "logreg_x3", "batch", "batch_big", "dense"],
+    ap.add_argument("--ncu-case-form", choices=["logreg", "logreg_x3", "batch", "batch_big", "batch_adj",
+                                                "batch_big_adj", "dense"],
                     help="no timing: a small case of another kernel (for ncu)")
     ap.add_argument("--ablations", action="store_true",
                     help="no contract line: the paper's ablations (MAMS only, fixed step, "
@@ -887,17 +904,19 @@ def main():
                 "hbm": {"achieved_gbs": hbm / (kms * 1e-3) / 1e9, "peak_gbs": pk["hbm_gbs"],
                         "frac": hbm / (kms * 1e-3) / 1e9 / pk["hbm_gbs"],
                         "basis": "16 B per coordinate and iteration (y, u read and written)"}}
-    if rec:
-        # [DRAM bytes per coordinate-iteration, warp instructions per coordinate-iteration]
-        # of one ncu capture of the small case, scaled by the coordinate-iterations of a launch
+    if rec and len(rec) >= 3:
+        # [DRAM bytes per coordinate-iteration, warp instructions per coordinate: LF step,
+        # proposal] from ncu captures of the batch's parts, scaled by a launch's work
         per_launch_ci = sum(p.M * p.d * (n_unadj[k] + (len(b.trace(k)) - 1 - n_unadj[k]))
                             for k, p in enumerate(probs)) / len(live)
         roofline["traffic"] = rec[0] * per_launch_ci
-        inst = rec[1] * sum(p.M * p.d * n_unadj[k] for k, p in enumerate(probs))
-        roofline["issue"] = {"warp_inst_per_coord_step": rec[1],
+        inst = sum(p.M * p.d * (rec[1] * n_unadj[k] + rec[2] * (len(b.trace(k)) - 1 - n_unadj[k]))
+                   for k, p in enumerate(probs))
+        roofline["issue"] = {"warp_inst_per_coord": {"lf_step": rec[1], "proposal": rec[2]},
                              "frac": inst / (kms * 1e-3) / (nsm * 4 * mhz * 1e6),
-                             "basis": "ncu smsp__inst_executed of the unadjusted small case; peak "
-                                      "%d SMs x 4 schedulers x 1 warp instruction per clock" % nsm}
+                             "basis": "ncu smsp__inst_executed of unadjusted and adjusted launches of the "
+                                      "batch's parts (profiles/batch_counters.txt); peak %d SMs x 4 "
+                                      "schedulers x 1 warp instruction per clock" % nsm}
 
     # every rank draws from the same seed: the ranks hold parts of one ensemble
     sharded = None if args.no_forms else _sharded_logreg(stream, world, rank, 600)

@@ -75,52 +75,29 @@ __device__ __forceinline__ void grp_bar(const Grp& G) {
 }
 
 // The group's warps' partials of value k sit at s[16 k + w] (w the warp in the
-// group, gw in {1, 2, 4, 8, 16}); they are read with float4 loads from gw = 4
-// on and added in warp order.
+// group, gw in {1, 2, 4, 8, 16}).  Lane l < gw of every warp reads partial l and
+// a butterfly over the warp adds them (the other lanes add zeros, exactly): every
+// lane of the group ends with the same bits, with one load and five shuffle-adds a lane in
+// place of gw sequential additions.
 __device__ __forceinline__ float part_sum(const float* s, int gw) {
-    if (gw < 4) return gw > 1 ? s[0] + s[1] : s[0];
-    const float4* s4 = reinterpret_cast<const float4*>(s);
-    float4 a = s4[0];
-    float t = a.x;
-    t += a.y;
-    t += a.z;
-    t += a.w;
-    for (int q = 1; q < gw / 4; ++q) {
-        a = s4[q];
-        t += a.x;
-        t += a.y;
-        t += a.z;
-        t += a.w;
-    }
+    const int lane = threadIdx.x & 31;
+    float t = lane < gw ? s[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
 }
 // float-float partials: high words at hi[w], low words at lo[w]
 __device__ __forceinline__ ff part_sum_ff(const float* hi, const float* lo, int gw) {
-    if (gw < 4) {
-        ff t{hi[0], lo[0]};
-        if (gw > 1) t = ff_add(t, ff{hi[1], lo[1]});
-        return t;
-    }
-    const float4* h4 = reinterpret_cast<const float4*>(hi);
-    const float4* l4 = reinterpret_cast<const float4*>(lo);
-    float4 a = h4[0], b = l4[0];
-    ff t{a.x, b.x};
-    t = ff_add(t, ff{a.y, b.y});
-    t = ff_add(t, ff{a.z, b.z});
-    t = ff_add(t, ff{a.w, b.w});
-    for (int q = 1; q < gw / 4; ++q) {
-        a = h4[q];
-        b = l4[q];
-        t = ff_add(t, ff{a.x, b.x});
-        t = ff_add(t, ff{a.y, b.y});
-        t = ff_add(t, ff{a.z, b.z});
-        t = ff_add(t, ff{a.w, b.w});
-    }
+    const int lane = threadIdx.x & 31;
+    ff t = lane < gw ? ff{hi[lane], lo[lane]} : ff_make(0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        t = ff_add(t, ff{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)});
     return t;
 }
 
-// Sum of NV values over the group: warp butterfly, then the group's warps in
-// order.  Two scratch buffers alternate, so one barrier per call suffices (a
+// Sum of NV values over the group: warp butterfly, then a butterfly over the
+// group's warp partials.  Two scratch buffers alternate, so one barrier per call suffices (a
 // warp cannot run two calls ahead of the others).  Every lane gets the same bits.
 template <int NV>
 __device__ __forceinline__ void gsum(Grp& G, float (&v)[NV]) {
