@@ -588,12 +588,12 @@ def ncu_case(adjusted: bool = False):
     import torch
     from paper_2601_16696_gb300 import build, laps, workloads
     build.build()
-    pr = workloads.banana(d=WORKLOAD["d"], M=WORKLOAD["M"], n_steps=WORKLOAD["n_steps"])
+    pr = workloads.banana(d=RESIDENT["d"], M=RESIDENT["M"], n_steps=RESIDENT["n_steps"])
     tg = laps.Target.from_problem(pr)
-    s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, force_switch_at=WORKLOAD["switch_at"])
+    s = laps.Sampler(tg, pr.M, n_total_steps=pr.n_steps, force_switch_at=RESIDENT["switch_at"])
     s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=0)  # resident launch 1
     if adjusted:
-        s.step(WORKLOAD["switch_at"])                                         # launch 2: to the switch
+        s.step(RESIDENT["switch_at"])                                         # launch 2: to the switch
         s.step(10)                                                            # launch 3: 10 proposals
     else:
         s.step(20)                                                            # resident launch 2
@@ -904,12 +904,13 @@ def main():
                 "hbm": {"achieved_gbs": hbm / (kms * 1e-3) / 1e9, "peak_gbs": pk["hbm_gbs"],
                         "frac": hbm / (kms * 1e-3) / 1e9 / pk["hbm_gbs"],
                         "basis": "16 B per coordinate and iteration (y, u read and written)"}}
-    if rec and len(rec) >= 3:
-        # [DRAM bytes per coordinate-iteration, warp instructions per coordinate: LF step,
-        # proposal] from ncu captures of the batch's parts, scaled by a launch's work
-        per_launch_ci = sum(p.M * p.d * (n_unadj[k] + (len(b.trace(k)) - 1 - n_unadj[k]))
-                            for k, p in enumerate(probs)) / len(live)
-        roofline["traffic"] = rec[0] * per_launch_ci
+    if rec and len(rec) >= 4:
+        # [DRAM bytes per coordinate: LF step; warp instructions per coordinate: LF step,
+        # proposal; DRAM bytes per coordinate: proposal] from ncu captures of the batch's
+        # parts, scaled by a run's work and averaged over its launches
+        bytes_run = sum(p.M * p.d * (rec[0] * n_unadj[k] + rec[3] * (len(b.trace(k)) - 1 - n_unadj[k]))
+                        for k, p in enumerate(probs))
+        roofline["traffic"] = bytes_run / len(live)
         inst = sum(p.M * p.d * (rec[1] * n_unadj[k] + rec[2] * (len(b.trace(k)) - 1 - n_unadj[k]))
                    for k, p in enumerate(probs))
         roofline["issue"] = {"warp_inst_per_coord": {"lf_step": rec[1], "proposal": rec[2]},

@@ -13,10 +13,11 @@
 //      problem has at least one group-round of chains per block, else just
 //      enough blocks for one round each, placed where the blocks carry the
 //      least work, so that no block runs a round with most of its groups idle.
-//      A chain is processed by a group of gw warps (gw = 1..16, chosen per
-//      problem from its d), with its coordinates in registers (CPL per lane)
-//      and group reductions by warp butterflies plus, across the group's
-//      warps, shared memory and a named barrier.  Per-coordinate sums of y
+//      A chain is processed by a group of L lanes (4, 8 or 16 lanes of a warp
+//      shared with other chains, or 1..16 whole warps; chosen per problem from
+//      its d), with its coordinates in registers (CPL per lane) and group
+//      reductions by butterflies over the group's lanes plus, across the
+//      group's warps, shared memory and a named barrier.  Per-coordinate sums of y
 //      and y^2 accumulate in shared memory per thread; the block writes one
 //      float-float column per problem (the register-resident kernel's layout);
 //   2. grid barrier; slice tasks (problem, block of coordinates) spread over
@@ -40,11 +41,12 @@ namespace laps {
 
 constexpr int kBT = 512;          // threads per block
 constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kMaxGrp = kBT / 4;   // chain groups of a block at 4 lanes per chain
 constexpr int kRed = 128;         // reduction scratch floats per group: 2 buffers x 4 values x 16 warps
 
 struct BatchArgs {
     const KParams* probs;  // [n]
-    const int* gw;         // [n] warps per chain
+    const int* gw;         // [n] lanes per chain: 4, 8, 16 (chains share a warp) or 32 x warps
     const int2* sched;     // [n] (first block, blocks) that hold the problem's chains; P.G = blocks
     const Coefs* coefs;
     int n;                 // problems
@@ -61,11 +63,11 @@ struct BatchArgs {
 
 // ---------------------------------------------------------------- chain groups
 struct Grp {
-    int gw;      // warps in the group
+    int gw;      // warps in the group (1 for a group of 4, 8, 16 or 32 lanes)
     int grp;     // group index in the block
     int wig;     // warp in the group
-    int gl;      // lane in the group (0 .. 32 gw - 1)
-    int lpc;     // lanes per chain = 32 gw
+    int gl;      // lane in the group (0 .. lpc - 1)
+    int lpc;     // lanes per chain: 4, 8, 16 (part of a warp) or 32 gw
     float* red;  // this group's reduction scratch
     int flip;    // scratch buffer in use
 };
@@ -104,7 +106,8 @@ __device__ __forceinline__ void gsum(Grp& G, float (&v)[NV]) {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int o = 16; o > 0; o >>= 1)
+            if (o < G.lpc) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     if (G.gw == 1) return;
     float* s = G.red + G.flip * 64;
     if ((threadIdx.x & 31) == 0)
@@ -121,7 +124,9 @@ __device__ __forceinline__ float gsum1(Grp& G, float v) {
     return a[0];
 }
 __device__ __forceinline__ ff gsum_ff(Grp& G, ff v) {
-    v = group_sum_ff<32>(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        if (o < G.lpc) v = ff_add(v, ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
     if (G.gw == 1) return v;
     float* s = G.red + G.flip * 64;
     if ((threadIdx.x & 31) == 0) {
@@ -191,6 +196,7 @@ template <int NV>
 __device__ __forceinline__ void gsum_mix(Grp& G, ff& a, float (&v)[NV]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+        if (o >= G.lpc) continue;  // uniform: every group of the block has lpc lanes
         a = ff_add(a, ff{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
 #pragma unroll
         for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
@@ -345,8 +351,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
     float* s_c = qbuf + 2 * kBT * CPL;             // [cap_pad] prec_i sigma_i^2 (0 past d)
     float* s_sg = s_c + B.cap_pad;                 // [cap_pad] preconditioner
     float* s_red = s_sg + B.cap_pad;               // [kBW][kRed]
-    ff* s_cs = reinterpret_cast<ff*>(s_red + kBW * kRed);  // [kBW][NCS]
-    ff* s_q = s_cs + kBW * NCS;                    // [NQ SL + NCS]
+    ff* s_cs = reinterpret_cast<ff*>(s_red + kBW * kRed);  // [kMaxGrp][NCS]
+    ff* s_q = s_cs + kMaxGrp * NCS;                // [NQ SL + NCS]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, b = blockIdx.x;
@@ -392,8 +398,15 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                 s_c[i] = i < P.d ? P.prec[i] * (sg * sg) : 0.0f;
                 s_sg[i] = sg;
             }
-            const int gw = B.gw[p], ng = kBW / gw;
-            Grp Gc{gw, warp / gw, warp % gw, (warp % gw) * 32 + lane, 32 * gw, s_red + (warp / gw) * kRed, 0};
+            // lanes per chain: 4, 8 or 16 (several chains share a warp) or a multiple of 32
+            const int Lp = B.gw[p], ng = kBT / Lp;
+            Grp Gc;
+            if (Lp >= 32) {
+                const int gw = Lp / 32;
+                Gc = Grp{gw, warp / gw, warp % gw, (warp % gw) * 32 + lane, Lp, s_red + (warp / gw) * kRed, 0};
+            } else {
+                Gc = Grp{1, warp * (32 / Lp) + lane / Lp, 0, lane % Lp, Lp, nullptr, 0};
+            }
             const int cap = Gc.lpc * CPL;
             // this thread's column slots, one float4 per coordinate block (conflict-free)
             float4* q0 = reinterpret_cast<float4*>(qbuf + (size_t)(0 * ng + Gc.grp) * cap);
@@ -413,7 +426,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
             const float dm1 = (float)(P.d - 1), inv_dm1 = 1.0f / (float)(P.d - 1);
             const bool pend = (B.mode == 1 && sH.phase == 1 && sH.p == 0);  // y still in x (switch)
             const int64_t m0 = (int64_t)slot * P.M / sc.y, m1 = (int64_t)(slot + 1) * P.M / sc.y;
-            for (int64_t mm = m0 + Gc.grp; mm < m1; mm += ng) {
+            // the same number of rounds for every group of the block (the groups of a
+            // warp share its shuffles); a group past its share's last chain runs on
+            // zeros and writes nothing
+            for (int64_t base = m0; base < m1; base += ng) {
+                const int64_t mm = base + Gc.grp;
+                const bool act = mm < m1;
                 const uint32_t m = (uint32_t)mm;
                 float y[CPL], u[CPL];
                 auto load = [&](const float* src, float(&v)[CPL]) {
@@ -421,7 +439,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                     for (int k = 0; k < NB; ++k) {
                         const int j = Gc.gl + Gc.lpc * k;
                         float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        if (j < P.nblk) a = *reinterpret_cast<const float4*>(src + (size_t)mm * P.d_pad + 4 * j);
+                        if (act && j < P.nblk) a = *reinterpret_cast<const float4*>(src + (size_t)mm * P.d_pad + 4 * j);
                         v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
                     }
                 };
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
 #pragma unroll
                     for (int k = 0; k < NB; ++k) {
                         const int j = Gc.gl + Gc.lpc * k;
-                        if (j < P.nblk)
+                        if (act && j < P.nblk)
                             *reinterpret_cast<float4*>(dst + (size_t)mm * P.d_pad + 4 * j) =
                                 make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     }
@@ -445,7 +463,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const int i = 4 * j + c;
-                            y[4 * k + c] = (j < P.nblk && i < P.d)
+                            y[4 * k + c] = (act && j < P.nblk && i < P.d)
                                                ? (P.x0 ? P.x0[(size_t)mm * P.d + i] : P.x0_scale * z[c])
                                                : 0.0f;
                         }
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                             for (int c = 0; c < 4; ++c) u[4 * k + c] = g[c] * inv;
                         }
                     }
-                    if (bad) atomicCAS(P.status, ST_OK, ST_NONFINITE);
+                    if (bad && act) atomicCAS(P.status, ST_OK, ST_NONFINITE);
                     store(P.y, y);
                     store(P.u, u);
                 } else {
@@ -546,7 +564,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                             }
                         if (pend) store(P.y, y);  // keep the accepted point in the new coordinates
                     }
-                    if (sH.phase == 0) {
+                    if (!act) {
+                    } else if (sH.phase == 0) {
                         if (bad) {
                             cs[CS_NBAD] = ff_add(cs[CS_NBAD], 1.0f);
                         } else {
@@ -560,6 +579,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                     }
                 }
                 // per-coordinate sums of y and y^2 (this thread's own slots)
+                if (act)
 #pragma unroll
                 for (int k = 0; k < NB; ++k) {
                     const int j = Gc.gl + Gc.lpc * k;
@@ -572,7 +592,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                     q1[j] = s;
                 }
             }
-            if (lane == 0 && Gc.wig == 0)
+            if (Gc.gl == 0)
 #pragma unroll
                 for (int k = 0; k < NCS; ++k) s_cs[Gc.grp * NCS + k] = cs[k];
             __syncthreads();
@@ -643,18 +663,21 @@ const void* batch_fn(int cpl) {
 
 size_t batch_smem(int cpl, int cap_pad, int SL) {
     return (size_t)2 * kBT * cpl * 4 + (size_t)2 * cap_pad * 4 + (size_t)kBW * kRed * 4 +
-           (size_t)kBW * NCS * sizeof(ff) + ((size_t)NQ * SL + NCS) * sizeof(ff);
+           (size_t)kMaxGrp * NCS * sizeof(ff) + ((size_t)NQ * SL + NCS) * sizeof(ff);
 }
 
 int batch_threads() { return kBT; }
 
-// warps per chain for dimension d with cpl coordinates per lane; 0 if it does not fit
+// lanes per chain for dimension d with cpl coordinates per lane: the fewest of
+// 4, 8, 16, 32, 64, ..., 512 that hold d (a chain of small d shares a warp with
+// others, a chain of large d spans warps), doubled `widen` times; 0 if none does
 int batch_gw(int64_t d, int cpl, int widen) {
-    int gw = 1;
-    while ((int64_t)32 * gw * cpl < ((d + 3) / 4) * 4 && gw < kBW) gw *= 2;
-    if ((int64_t)32 * gw * cpl < ((d + 3) / 4) * 4) return 0;
-    for (int k = 0; k < widen && gw < kBW; ++k) gw *= 2;
-    return gw;
+    const int64_t dp = ((d + 3) / 4) * 4;
+    int L = 4;
+    while ((int64_t)L * cpl < dp && L < kBT) L *= 2;
+    if ((int64_t)L * cpl < dp) return 0;
+    for (int k = 0; k < widen && L < kBT; ++k) L *= 2;
+    return L;
 }
 
 cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, const int2* sched,
@@ -702,10 +725,10 @@ cudaError_t batch_launch(int cpl, int G, const KParams* probs, const int* gw, co
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-// A block runs one problem at a time with all its ng = 16 / gw chain groups; a
-// round (ng chains side by side) costs about ceil(nblk / (32 gw)) passes over
-// the lanes' coordinate blocks whatever gw is, so that is a problem's cost per
-// round.  A problem with at least ng chains per block is spread over every
+// A block runs one problem at a time with all its ng = 512 / L chain groups of
+// L lanes; a round (ng chains side by side) costs about ceil(nblk / L) passes
+// over the lanes' coordinate blocks whatever L is, so that is a problem's cost
+// per round.  A problem with at least ng chains per block is spread over every
 // block (rounds = ceil(ceil(M / G) / ng) each).  Any other problem gets
 // ceil(M / ng) blocks, one round each, at the place where the most loaded of
 // those blocks carries the least work so far (larger problems placed first).
@@ -713,10 +736,10 @@ void batch_schedule(const int64_t* d, const int64_t* M, int n, int cpl, int wide
     std::vector<double> load(G, 0.0);
     std::vector<int> order;
     auto cost = [&](int k, int& ng) {
-        const int gw = batch_gw(d[k], cpl, widen);
-        ng = kBW / std::max(gw, 1);
+        const int L = std::max(batch_gw(d[k], cpl, widen), 4);  // lanes per chain
+        ng = kBT / L;
         const int64_t nblk = (d[k] + 3) / 4;
-        return (double)((nblk + 32 * gw - 1) / (32 * gw));
+        return (double)((nblk + L - 1) / L);
     };
     for (int k = 0; k < n; ++k) {
         int ng = 1;

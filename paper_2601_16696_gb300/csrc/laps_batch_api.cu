@@ -48,7 +48,7 @@ struct laps_batch {
     Hyper* hyper = nullptr;      // [n] device, one block of phase machines
     Hyper* h_hyper = nullptr;    // [n] pinned host copy
     KParams* d_probs = nullptr;  // [n] parameter blocks the kernel reads
-    int* d_gw = nullptr;         // [n] warps per chain
+    int* d_gw = nullptr;         // [n] lanes per chain (4 .. 512)
     int2* d_sched = nullptr;     // [n] blocks that hold each problem's chains
     std::vector<int2> sched;     // host copy
     Coefs* d_coefs = nullptr;
