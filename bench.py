@@ -327,7 +327,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": _batch_config(probs, {"parallelism": "host cores (the oracle)"}),
+            "config": _batch_config(probs),
+            "run": {"parallelism": "host cores (the oracle)"},
             "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v,
                                                                                     "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -928,10 +929,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _batch_config(probs, {
-                "chain_grads_per_run": chain_grads, "shape": sh, "iters_per_launch": K_ipl,
-                "integrators": sorted({("MN4" if st["integrator"] == 2 else "MN2") for st in sts}),
-                "parallelism": "replicas" if world > 1 else "1 GPU"}),
+            "config": _batch_config(probs),
+            "run": {"chain_grads_per_run": chain_grads, "shape": sh, "iters_per_launch": K_ipl,
+                    "integrators": sorted({("MN4" if st["integrator"] == 2 else "MN2") for st in sts}),
+                    "parallelism": "replicas" if world > 1 else "1 GPU"},
             "time_to_b2": {"ms": statistics.mean(reached) if reached else None, "b2": "b2_avg",
                            "threshold": 0.01, "over": "every problem", "runs_reached": len(reached),
                            "of": len(b2)},

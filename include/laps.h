@@ -203,7 +203,7 @@ laps_status laps_target_create(const laps_target_desc* desc, laps_target** out);
 void laps_target_destroy(laps_target* tg);
 
 /* log p and grad log p of M points: x device [M][d], logp device [M],
- * grad device [M][d].  Forward and hand-written backward of the target (the
+ * grad device [M][d] (M = 0: nothing is done and the pointers may be NULL).  Forward and hand-written backward of the target (the
  * kernels the sampler uses), FP32 in and out with compensated sums. */
 laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
                                   float* logp, float* grad, void* stream);
@@ -334,7 +334,8 @@ laps_status laps_run_noalloc(const laps_target_desc* desc, int64_t M, const laps
  * [n_ranks][bytes], in rank order, stream-ordered on `stream` (e.g. an NCCL
  * all-gather), and return 0; it is called on the host thread that enqueues the
  * iteration, once per iteration (also for the initialisation).  With
- * n_ranks = 1 it may be NULL (a local copy).  Served on the streamed path:
+ * n_ranks = 1 it may be NULL (a local copy), and that rank holds the whole
+ * ensemble (m0 = 0, M_local = M_total).  Served on the streamed path:
  * LOGREG and USER targets, GAUSS_DENSE beyond d = 128 or with dense_streamed;
  * other targets return LAPS_ERR_UNSUPPORTED.  With one rank the results equal
  * laps_create's bit for bit. */

@@ -528,6 +528,8 @@ laps_status laps_create_sharded(const laps_target* tg, int64_t M_local, const la
         return fail(LAPS_ERR_INVALID_ARG, "shard: need 0 <= rank < n_ranks and 0 <= m0, m0 + M_local <= M_total");
     if (sh->n_ranks > 1 && !sh->allgather)
         return fail(LAPS_ERR_INVALID_ARG, "shard: more than one rank needs an allgather callback");
+    if (sh->n_ranks == 1 && (sh->m0 != 0 || M_local != sh->M_total))
+        return fail(LAPS_ERR_INVALID_ARG, "shard: a single rank holds the whole ensemble (m0 = 0, M_local = M_total)");
     const bool streamed = streamed_kind(tg->kind) &&
                           !(tg->kind == TGT_GAUSS_DENSE && tg->d_pad <= kDenseResidentMax && !cfg->dense_streamed);
     if (!streamed)

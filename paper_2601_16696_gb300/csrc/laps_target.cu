@@ -236,7 +236,7 @@ extern "C" laps_status laps_target_status(laps_target* tg) {
 
 extern "C" laps_status laps_target_logp_grad_prec(const laps_target* tg, const float* x, int64_t M,
                                                   float* logp, float* grad, int precision, void* stream) {
-    if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (!tg || M < 0 || (M > 0 && (!x || !logp || !grad))) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (precision == LAPS_FP32) return laps_target_logp_grad(tg, x, M, logp, grad, stream);
     if (precision != LAPS_MIXED && precision != LAPS_BF16X3) return fail(LAPS_ERR_INVALID_ARG, "unknown precision");
     if (tg->kind != TGT_LOGREG) return fail(LAPS_ERR_UNSUPPORTED, "mixed precision applies to LOGREG only");
@@ -247,7 +247,7 @@ extern "C" laps_status laps_target_logp_grad_prec(const laps_target* tg, const f
 
 extern "C" laps_status laps_target_logp_grad(const laps_target* tg, const float* x, int64_t M,
                                              float* logp, float* grad, void* stream) {
-    if (!tg || !x || !logp || !grad || M < 0) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    if (!tg || M < 0 || (M > 0 && (!x || !logp || !grad))) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
     if (M == 0) return LAPS_OK;
     if (tg->kind == TGT_USER) {
         const int r = tg->desc.user_fn(x, M, tg->d, logp, grad, stream, tg->desc.user_data);

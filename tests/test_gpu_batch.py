@@ -187,3 +187,27 @@ def test_batch_rejects_bad_problems(L):
     with pytest.raises(L.LapsError) as e:
         L.Batch([pr], n_total_steps=5)
     assert e.value.status == 1
+
+
+def test_batch_extreme_shapes(L, ora):
+    """The largest dimension the batch serves (d = 10240) beside the smallest
+    (d = 2), with 2 and 3 chains: first steps within 1e-5 of the oracle."""
+    probs = [W.gauss_diag(d=10240, M=3, n_steps=20, x0_scale=1.0, var_lo=0.1, var_hi=10.0, seed=21),
+             W.gauss_diag(d=2, M=2, n_steps=20, x0_scale=1.0, var_lo=0.5, var_hi=2.0, seed=22)]
+    b = L.Batch(probs, n_total_steps=20, fixed_eps=0.05)
+    b.init(seed=17)
+    b.step(3)
+    for k, pr in enumerate(probs):
+        r = _ora(ora, pr, 17, k, fixed_eps=0.05)
+        r.iterate(3)
+        assert _rel(b.sample(k).double().cpu().numpy(), r.x()) <= 1e-5, k
+
+
+def test_empty_calls_are_no_ops(L):
+    """M = 0 points and n = 0 counters: nothing to do, status OK."""
+    pr = W.gauss_diag(d=5, M=2, n_steps=5)
+    tg = L.Target.from_problem(pr)
+    lp, g = tg.logp_grad(torch.empty(0, 5, dtype=torch.float32, device="cuda"))
+    assert lp.numel() == 0 and g.numel() == 0
+    out = L.philox(torch.empty(0, 4, dtype=torch.int32, device="cuda"), 1)
+    assert out.numel() == 0

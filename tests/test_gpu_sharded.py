@@ -180,3 +180,6 @@ def test_sharded_rejections(L):
     with pytest.raises(L.LapsError) as e:
         L.Sampler(ltg, 8, n_total_steps=10, shard=(12, 6, 0, 2, None))  # chains past M_total, no callback
     assert e.value.status == 1
+    with pytest.raises(L.LapsError) as e:
+        L.Sampler(ltg, 8, n_total_steps=10, shard=(16, 0, 0, 1, None))  # one rank short of its ensemble
+    assert e.value.status == 1
