@@ -272,11 +272,15 @@ __device__ __forceinline__ void g_b_apply(const Grp& G, const KParams& P, float 
     dl = ff_add(dl, dm1 * (delta + log1pf(-0.5f * om * opz * (1.0f - eu))));
 }
 
+// dl collects the B maps' kinetic-energy changes (per chain, the same on every
+// lane); dlA each lane's part of the A maps' log-p changes, reduced over the
+// group only when the energy error is read (check: the step's or the
+// proposal's end), together with the last O map's norm.
 template <int CPL>
 __device__ __forceinline__ void g_step(const KParams& P, const PhiloxKeys& RK, Grp& G, const Coefs& CF, int integ,
                                        float eps, float c1, float c2s, uint32_t m, uint32_t t, float (&y)[CPL],
-                                       float (&u)[CPL], ff& dl, float inv_dm1, float dm1, const float4* s_c4,
-                                       bool check, bool& bad) {
+                                       float (&u)[CPL], ff& dl, ff& dlA, float inv_dm1, float dm1,
+                                       const float4* s_c4, bool check, bool& bad) {
     const int K = CF.K[integ];
     float s[3] = {0.0f, 0.0f, 0.0f};
     g_o_mix<CPL, true>(P, RK, G, m, t, TAG_O1, c1, c2s, u, y, s_c4, s);
@@ -310,9 +314,8 @@ __device__ __forceinline__ void g_step(const KParams& P, const PhiloxKeys& RK, G
                     v2[1] = fmaf(g, u[q], v2[1]);
                 }
             }
-            ff dlp = ff_make(part);
-            gsum_mix<2>(G, dlp, v2);
-            dl = ff_add(dl, ff_neg(dlp));
+            gsum<2>(G, v2);
+            dlA = ff_add(dlA, -part);
             gg = v2[0];
             gu = v2[1];
         }
@@ -320,12 +323,14 @@ __device__ __forceinline__ void g_step(const KParams& P, const PhiloxKeys& RK, G
     float s2[3] = {0.0f, 0.0f, 0.0f};
     g_o_mix<CPL, false>(P, RK, G, m, t, TAG_O2, c1, c2s, u, y, s_c4, s2);
     if (check) {
-        float f = isfinite(dl.hi) ? 0.0f : 1.0f;
+        float f = (isfinite(dl.hi) && isfinite(dlA.hi)) ? 0.0f : 1.0f;
 #pragma unroll
         for (int q = 0; q < CPL; ++q)
             if (!(isfinite(y[q]) && isfinite(u[q]))) f = 1.0f;
         float r[2] = {s2[0], f};
-        gsum<2>(G, r);
+        gsum_mix<2>(G, dlA, r);  // the A maps' log-p change of the chain, with the O map's norm
+        dl = ff_add(dl, dlA);
+        dlA = ff_make(0.0f);
         s2[0] = r[0];
         bad = r[1] > 0.0f;
     } else {
@@ -508,11 +513,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) y[4 * k + c] = y[4 * k + c] / s_sg[4 * j + c];
                         }
-                    ff dl = ff_make(0.0f);
+                    ff dl = ff_make(0.0f), dlA = ff_make(0.0f);
                     const int integ = sH.phase == 0 ? INTEG_LF : sH.integ;
                     bool bad = false;
                     if (sH.phase == 0) {
-                        g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, (uint32_t)sH.t, y, u, dl, inv_dm1, dm1,
+                        g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, (uint32_t)sH.t, y, u, dl, dlA, inv_dm1, dm1,
                                     s_c4, true, bad);
                     } else {
                         // App. F step 2: u uniform on the sphere, then N steps
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                         for (int q = 0; q < CPL; ++q) u[q] *= inv;
                         const uint32_t t0 = (uint32_t)sH.t;
                         for (int n = 0; n < P.N; ++n)
-                            g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, t0 + n, y, u, dl, inv_dm1, dm1, s_c4,
+                            g_step<CPL>(P, B.keys, Gc, CF, integ, eps, c1, c2s, m, t0 + n, y, u, dl, dlA, inv_dm1, dm1, s_c4,
                                         n == P.N - 1, bad);
                     }
                     bool keep = !bad;

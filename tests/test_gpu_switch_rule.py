@@ -4,8 +4,8 @@ fluctuations"; the exit test of Alg. 1's unadjusted loop) firing by itself.
 The window statistic delta_i = sqrt(Var_window[E x_i^2]) / mean_window[E x_i^2]
 over the last T = ceil(0.2 n_total_steps) steps, and the switch at the first
 full-window step where max_i delta_i < switch_tol, are computed by the device
-window ring and slice owners; the oracle recomputes them from its stored
-window every step.  Both runs start from the same ensemble and draw the same
+window ring and slice owners (register-resident, batched and streamed paths);
+the oracle recomputes them from its stored window every step.  Both runs start from the same ensemble and draw the same
 Philox stream, and no run here forces the switch.
 
 - With the step size held fixed (the fixed-step comparison of App. A), the
@@ -59,7 +59,18 @@ class _BatchRun:
         return self.b.trace(0)
 
 
+def _dense(pr):
+    """The same Gaussian given by its precision matrix (the streamed path's
+    dense-precision target, GAUSS_DENSE with dense_streamed)."""
+    pr.kind = W.GAUSS_DENSE
+    pr.prec = np.diag(pr.prec)
+    return pr
+
+
 def _pair(L, ora, pr, seed, path="resident", **cfg):
+    if path == "streamed":
+        pr = _dense(pr)
+        cfg = dict(cfg, dense_streamed=1)
     if path == "batch":
         s = _BatchRun(L, pr, seed, **cfg)
     else:
@@ -69,6 +80,7 @@ def _pair(L, ora, pr, seed, path="resident", **cfg):
         s.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=seed)
         s._tg = tg
     ot = ora.OracleTarget(pr.kind, pr.d, prec=pr.prec)
+    cfg.pop("dense_streamed", None)
     r = ora.OracleLAPS(ot, pr.x0, seed=seed, truth=(pr.Ex2, pr.Varx2), n_total_steps=pr.n_steps,
                        **cfg)
     return s, r
@@ -99,6 +111,8 @@ FIXED = {
     "resident_d100_M4096": ("resident", dict(d=100, M=4096, n_steps=2000), 0,
                             dict(fixed_eps=0.3, switch_tol=0.05)),
     "batch_d10_M65536": ("batch", dict(M=65536, **D10), 0, dict(fixed_eps=0.6)),
+    # the streamed path's finalise kernel (the same Gaussian as a dense precision matrix)
+    "streamed_d10_M65536": ("streamed", dict(M=65536, **D10), 0, dict(fixed_eps=0.6)),
 }
 # adaptive runs: seeds whose switch step the oracle and its binary32 variant
 # agree on, with max delta more than 1% away from the threshold on both sides.
