@@ -91,6 +91,19 @@ def _max_over_ranks(x: float) -> float:
     return float(t.item())
 
 
+def _sum_over_ranks(x: float) -> float:
+    """The sum of x over the ranks of the process group; x itself without a
+    group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -748,6 +761,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="laps", choices=["laps", "reference"])
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "problems"],
+                    help="N > 1: every rank runs the whole batch (replicas, weak scaling) or its "
+                         "share of the batch's problems (laps_batch_partition, strong scaling)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="runs timed end to end (default: a quarter of --steps, at least 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -787,7 +803,18 @@ def main():
     K_ipl = BATCH["iters_per_launch"]
 
     # ---- the batch: initial positions in one device buffer (one H2D copy for e2e)
-    probs = workloads.batch64(n_steps=BATCH["n_steps"])
+    all_probs = workloads.batch64(n_steps=BATCH["n_steps"])
+    by_problems = args.partition == "problems" and world > 1
+    if by_problems:
+        # this rank's share; the problems keep their Philox ids of the whole batch
+        ids = laps.partition_problems(all_probs, world)[rank]
+        if not ids:
+            raise SystemExit("--partition problems: rank %d owns no problem (%d ranks, %d problems)"
+                             % (rank, world, len(all_probs)))
+        seed_base = 0
+    else:
+        ids = list(range(len(all_probs)))
+    probs = [all_probs[k] for k in ids]
     sizes = [p.M * p.d for p in probs]
     offs = np.concatenate([[0], np.cumsum(sizes)])
     total = int(offs[-1])
@@ -800,7 +827,7 @@ def main():
     views = [dataclasses.replace(p, x0=x0_dev[int(o):int(o) + p.M * p.d].view(p.M, p.d))
              for p, o in zip(probs, offs)]
     outs = [out_dev[int(o):int(o) + p.M * p.d].view(p.M, p.d) for p, o in zip(probs, offs)]
-    b = laps.Batch(views, n_total_steps=BATCH["n_steps"], force_switch_at=BATCH["switch_at"])
+    b = laps.Batch(views, n_total_steps=BATCH["n_steps"], force_switch_at=BATCH["switch_at"], ids=ids)
     for k, p in enumerate(probs):
         b.set_truth(k, p.Ex2, p.Varx2)
     b.init(seed=seed_base)
@@ -850,8 +877,11 @@ def main():
     barrier()
     assert all(st["done"] for st in sts), "a problem did not finish"
     chain_grads = sum(p.M * st["grads"] for p, st in zip(probs, sts))
+    # the units every rank processed: replicas run the whole batch each, a
+    # partition's ranks their shares of one batch
+    job_grads = _sum_over_ranks(float(chain_grads))
     ms = _max_over_ranks(statistics.mean(ts))
-    value = world * chain_grads / (ms * 1e-3)
+    value = job_grads / (ms * 1e-3)
     clocks = clk.summary()
 
     # ---- end to end through the batch entry points with host buffers
@@ -860,7 +890,7 @@ def main():
     te, _, _ = timed(e2e_run, n_e2e, seed_base + 200)
     barrier()
     e2e_ms = _max_over_ranks(statistics.mean(te))
-    e2e = {"value": world * chain_grads / (e2e_ms * 1e-3), "unit": UNIT,
+    e2e = {"value": job_grads / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": x0_host.numel() * 4, "d2h_bytes_per_step": out_host.numel() * 4,
            "ms_per_step": e2e_ms, "steps": n_e2e}
 
@@ -928,11 +958,14 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _batch_config(probs),
-            "run": {"chain_grads_per_run": chain_grads, "shape": sh, "iters_per_launch": K_ipl,
+            "scaling": "strong" if by_problems else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _batch_config(all_probs),
+            "run": {"chain_grads_per_run": job_grads if by_problems else chain_grads, "shape": sh,
+                    "iters_per_launch": K_ipl,
                     "integrators": sorted({("MN4" if st["integrator"] == 2 else "MN2") for st in sts}),
-                    "parallelism": "replicas" if world > 1 else "1 GPU"},
+                    "parallelism": ("problems over %d ranks (laps_batch_partition; rank 0 runs %d of %d)"
+                                    % (world, len(probs), len(all_probs))) if by_problems
+                                   else "replicas" if world > 1 else "1 GPU"},
             "time_to_b2": {"ms": statistics.mean(reached) if reached else None, "b2": "b2_avg",
                            "threshold": 0.01, "over": "every problem", "runs_reached": len(reached),
                            "of": len(b2)},
@@ -948,7 +981,8 @@ def main():
             line["forms"] = forms
             line["measured_peaks"] = _probe_peaks(stream)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = _batch_oracle(probs, total_chain_grads=chain_grads)
+            line["cpu_baseline"] = _batch_oracle(all_probs, total_chain_grads=job_grads if by_problems
+                                                 else chain_grads)
             if not args.no_forms:
                 line["cpu_baseline"]["other_workloads"] = _oracle_rates()
         print(json.dumps(line))

@@ -24,7 +24,7 @@
  *    void*; NULL is the legacy default stream).  These calls block the host:
  *     - set-up calls that allocate or copy host arrays in: laps_target_create,
  *       laps_create, laps_set_truth, laps_batch_create, laps_batch_set_truth,
- *       laps_batch_set_shape (device-synchronous);
+ *       laps_batch_set_shape, laps_batch_set_ids (device-synchronous);
  *     - calls that read results back: laps_get_stats, laps_get_trace,
  *       laps_checkpoint, laps_restore, laps_adapt_freeze, laps_target_status,
  *       laps_batch_get_stats, laps_batch_get_trace, laps_batch_tune,
@@ -39,7 +39,7 @@
  *    register-resident path, laps_sample, laps_get_state, laps_philox,
  *    laps_normals, laps_target_logp_grad[_prec], laps_batch_init,
  *    laps_batch_step, laps_batch_run, laps_batch_sample) only enqueues work
- *    and returns.
+ *    and returns; laps_batch_partition is host arithmetic and touches no GPU.
  *  - Errors raised inside a kernel (a bounded wait that expired, a bad
  *    parameter) are latched in a device status word and returned by the next
  *    call that reads it (laps_get_stats, or any synchronising call).
@@ -432,6 +432,25 @@ laps_status laps_batch_get_stats(laps_batch* b, int k, laps_stats* out);
 laps_status laps_batch_get_trace(laps_batch* b, int k, laps_trace_row* rows, int cap, int* n);
 /* Problem k's chain positions x = sigma o y: x_out device [M_k][d_k]. */
 laps_status laps_batch_sample(laps_batch* b, int k, float* x_out, void* stream);
+
+/* ---- a batch split over ranks by problems ---------------------------------
+ * The problems of a batch are independent, so ranks (one GPU each) can run
+ * disjoint sub-batches with no exchange at all.  laps_batch_partition assigns
+ * problem k (d[k], M[k], host arrays [n]) to rank owner[k] (host [n], written)
+ * by longest processing time first on the cost d_pad M: problems by falling
+ * cost, ties by lower index, each to the least-loaded rank, ties by lower
+ * rank.  Deterministic, so every rank computes the same owner array.  The
+ * largest rank load is at most the total / n_ranks plus the largest cost.
+ * INVALID_ARG on null arrays, n < 1, n_ranks < 1 or a non-positive d or M.
+ *
+ * laps_batch_set_ids gives problem k of b the Philox problem id ids[k] (host
+ * [n] int32, distinct, in [0, 2^24); the default is k), so a problem drawn
+ * into a sub-batch under its index in the whole batch draws the same noise as
+ * in the whole batch.  Device-synchronous (it rewrites the parameter blocks);
+ * takes effect at the next launch.  INVALID_ARG on null arguments, ids out of
+ * range or repeated. */
+laps_status laps_batch_partition(const int64_t* d, const int64_t* M, int n, int n_ranks, int32_t* owner);
+laps_status laps_batch_set_ids(laps_batch* b, const int32_t* ids);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,7 @@ struct laps_batch {
     int n = 0;
     laps_config cfg{};
     std::vector<BProb> P;
+    std::vector<uint32_t> ids;   // Philox problem id of each problem (default: its index)
     std::vector<void*> allocs;
     Hyper* hyper = nullptr;      // [n] device, one block of phase machines
     Hyper* h_hyper = nullptr;    // [n] pinned host copy
@@ -122,7 +123,7 @@ KParams make_params(const laps_batch* b, int k) {
     P.timeout_ns = g.barrier_timeout_ns;
     P.seed_lo = (uint32_t)b->seed;
     P.seed_hi = (uint32_t)(b->seed >> 32);
-    P.pid = (uint32_t)k;
+    P.pid = b->ids[k];
     P.G = b->sched.empty() ? b->G : b->sched[k].y;  // columns the slice owners add
     P.qpp = 1;
     P.smax = b->SL;
@@ -278,6 +279,8 @@ laps_status laps_batch_create(const laps_problem* probs, int n, const laps_confi
     b->n = n;
     b->cfg = *cfg;
     b->P.resize(n);
+    b->ids.resize(n);
+    for (int k = 0; k < n; ++k) b->ids[k] = (uint32_t)k;
     auto alloc = [&](void** p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) return false;
         b->allocs.push_back(*p);
@@ -489,6 +492,41 @@ laps_status laps_batch_set_shape(laps_batch* b, const laps_batch_shape* s) {
     if (!b || !s || s->slice < 1 || s->slice > 4096 || s->widen < 0 || s->widen > 4)
         return fail(LAPS_ERR_INVALID_ARG, "bad shape");
     return set_shape(b, s->coords_per_lane, s->widen, s->slice);
+}
+
+laps_status laps_batch_set_ids(laps_batch* b, const int32_t* ids) {
+    if (!b || !ids) return fail(LAPS_ERR_INVALID_ARG, "null argument");
+    std::vector<int32_t> seen(ids, ids + b->n);
+    std::sort(seen.begin(), seen.end());
+    for (int k = 0; k < b->n; ++k) {
+        if (seen[k] < 0 || seen[k] >= (1 << 24)) return fail(LAPS_ERR_INVALID_ARG, "problem ids must be in [0, 2^24)");
+        if (k > 0 && seen[k] == seen[k - 1]) return fail(LAPS_ERR_INVALID_ARG, "problem ids must be distinct");
+    }
+    for (int k = 0; k < b->n; ++k) b->ids[k] = (uint32_t)ids[k];
+    return upload(b);
+}
+
+laps_status laps_batch_partition(const int64_t* d, const int64_t* M, int n, int n_ranks, int32_t* owner) {
+    if (!d || !M || !owner || n < 1 || n_ranks < 1) return fail(LAPS_ERR_INVALID_ARG, "bad argument");
+    std::vector<int64_t> cost(n);
+    for (int k = 0; k < n; ++k) {
+        if (d[k] < 1 || M[k] < 1) return fail(LAPS_ERR_INVALID_ARG, "problem d and M must be positive");
+        cost[k] = (d[k] + 3) / 4 * 4 * M[k];
+    }
+    // longest processing time first: problems by falling cost (ties: lower
+    // index first), each to the rank with the least load (ties: lower rank)
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<int64_t> load(n_ranks, 0);
+    for (int k : order) {
+        int r = 0;
+        for (int q = 1; q < n_ranks; ++q)
+            if (load[q] < load[r]) r = q;
+        owner[k] = r;
+        load[r] += cost[k];
+    }
+    return LAPS_OK;
 }
 
 laps_status laps_batch_get_stats(laps_batch* b, int k, laps_stats* o) {

@@ -59,10 +59,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
     return c;
 }
 
-// ((r >> 9) + 1/2) 2^-23 = (r >> 9) 2^-23 + 2^-24: a binary32 value in (0, 1), exact
-// (one fused multiply-add of exact terms).
+// ((r >> 9) + 1/2) 2^-23 = (r >> 9) 2^-23 + 2^-24: a binary32 value in (0, 1), exact.
+// The 23 bits become the fraction of 1 + (r >> 9) 2^-23 in [1, 2); subtracting
+// 1 - 2^-24 (0x3F7FFFFF) is exact, since the result (2 (r >> 9) + 1) 2^-24 has a
+// 24-bit significand.  No integer-to-float conversion.
 __device__ __forceinline__ float u01(uint32_t r) {
-    return fmaf(static_cast<float>(r >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+    return __uint_as_float(0x3F800000u | (r >> 9)) - 0.99999994039535522f;
 }
 
 // sqrt(-2 ln u) for u in (0, 1): the argument is > 0, so x rsqrt(x) is finite;

@@ -163,6 +163,9 @@ SIGNATURES = {
     "laps_batch_get_trace": (C.c_int, [_vp, C.c_int, C.POINTER(TraceRow), C.c_int,
                                        C.POINTER(C.c_int)]),
     "laps_batch_sample": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "laps_batch_partition": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int, C.c_int,
+                                       C.POINTER(C.c_int32)]),
+    "laps_batch_set_ids": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
 }
 
 
@@ -493,12 +496,27 @@ def noalloc_setup() -> None:
     _check(lib().laps_run_noalloc(None, 0, None, None, 0.0, 0, None, None, None))
 
 
+def partition_problems(problems, n_ranks: int) -> list:
+    """laps_batch_partition: the problem indices each of n_ranks ranks runs
+    (``problems``: objects with d and M)."""
+    n = len(problems)
+    d = np.array([int(p.d) for p in problems], dtype=np.int64)
+    M = np.array([int(p.M) for p in problems], dtype=np.int64)
+    owner = np.zeros(n, dtype=np.int32)
+    _check(lib().laps_batch_partition(d.ctypes.data_as(C.POINTER(C.c_int64)),
+                                      M.ctypes.data_as(C.POINTER(C.c_int64)), n, n_ranks,
+                                      owner.ctypes.data_as(C.POINTER(C.c_int32))))
+    return [[k for k in range(n) if owner[k] == r] for r in range(n_ranks)]
+
+
 class Batch:
     """Independent diagonal-Gaussian problems in one persistent launch
-    (laps_batch_*).  ``problems``: objects with d, M, prec (and optionally x0)."""
+    (laps_batch_*).  ``problems``: objects with d, M, prec (and optionally x0);
+    ``ids``: their Philox problem ids (default 0 .. n-1; a rank's share of a
+    partitioned batch passes the problems' indices in the whole batch)."""
 
     def __init__(self, problems, config: Config | None = None, x0_scale: float = 1.0,
-                 use_x0: bool = True, **cfg_kw):
+                 use_x0: bool = True, ids=None, **cfg_kw):
         self.config = config if config is not None else default_config(**cfg_kw)
         self.n = len(problems)
         self.dims = [(int(p.d), int(p.M)) for p in problems]
@@ -516,6 +534,11 @@ class Batch:
         h = C.c_void_p()
         _check(lib().laps_batch_create(arr, self.n, C.byref(self.config), C.byref(h)))
         self._h = h
+        if ids is not None:
+            a = np.ascontiguousarray(ids, dtype=np.int32)
+            if a.shape != (self.n,):
+                raise ValueError("ids must hold one id per problem")
+            _check(lib().laps_batch_set_ids(self._h, a.ctypes.data_as(C.POINTER(C.c_int32))))
 
     def __del__(self):
         h = getattr(self, "_h", None)

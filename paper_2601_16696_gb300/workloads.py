@@ -197,16 +197,25 @@ def logreg_reference_moments(path: str | None = None):
     return a[:, 1].copy(), a[:, 2].copy()
 
 
+def batch64_shapes(seed: int = 0, n_small: int = 64):
+    """(d, condition number, M) of batch64's small problems: d log-uniform in
+    [10, 2000], condition log-uniform in [1e2, 1e4], M in {512, ..., 4096}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_small):
+        d = int(round(np.exp(rng.uniform(np.log(10), np.log(2000)))))
+        kappa = float(np.exp(rng.uniform(np.log(1e2), np.log(1e4))))
+        M = int(rng.choice([512, 1024, 2048, 4096]))
+        out.append((d, kappa, M))
+    return out
+
+
 def batch64(seed: int = 0, n_small: int = 64, big_d: int = 10000, big_M: int = 16384,
             big_kappa: float = 1e4, n_steps: int = 2000, with_big: bool = True,
             x0_scale: float = 1.0):
     """List of Problems: n_small Gaussians of uneven shape plus one large one."""
-    rng = np.random.default_rng(seed)
     probs = []
-    for k in range(n_small):
-        d = int(round(np.exp(rng.uniform(np.log(10), np.log(2000)))))
-        kappa = float(np.exp(rng.uniform(np.log(1e2), np.log(1e4))))
-        M = int(rng.choice([512, 1024, 2048, 4096]))
+    for k, (d, kappa, M) in enumerate(batch64_shapes(seed, n_small)):
         pr = gauss_diag(d=d, M=M, n_steps=n_steps, x0_scale=x0_scale,
                         var_lo=kappa ** -0.5, var_hi=kappa ** 0.5, seed=seed * 1000 + k + 1)
         pr.name = "batch%d_d%d_M%d" % (k, d, M)

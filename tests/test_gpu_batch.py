@@ -211,3 +211,31 @@ def test_empty_calls_are_no_ops(L):
     assert lp.numel() == 0 and g.numel() == 0
     out = L.philox(torch.empty(0, 4, dtype=torch.int32, device="cuda"), 1)
     assert out.numel() == 0
+
+
+def test_batch_partitioned_by_problems(L, ora):
+    """A batch split over two ranks by laps_batch_partition (the ranks emulated
+    one after the other on this GPU; the sub-batches exchange nothing): each
+    sub-batch carries its problems' ids of the whole batch, so every problem
+    follows the oracle run with pid = its index in the whole batch (first
+    steps at a fixed step size) and the whole batch's run of it."""
+    probs = _probs(SPEC, 40)
+    shares = L.partition_problems(probs, 2)
+    assert sorted(shares[0] + shares[1]) == list(range(len(probs))) and all(shares)
+    whole = L.Batch(probs, n_total_steps=40, fixed_eps=0.05)
+    whole.init(seed=21)
+    whole.step(4)
+    for share in shares:
+        sub = L.Batch([probs[k] for k in share], n_total_steps=40, fixed_eps=0.05, ids=share)
+        sub.init(seed=21)
+        sub.step(4)
+        for j, k in enumerate(share):
+            r = _ora(ora, probs[k], 21, k, fixed_eps=0.05)
+            r.iterate(4)
+            xs = sub.sample(j).double().cpu().numpy()
+            assert _rel(xs, r.x()) <= 1e-5, (k, share)
+            assert _rel(xs, whole.sample(k).double().cpu().numpy()) <= 1e-5, (k, share)
+    with pytest.raises(L.LapsError):
+        L.Batch(probs[:2], n_total_steps=40, ids=[3, 3])
+    with pytest.raises(L.LapsError):
+        L.Batch(probs[:1], n_total_steps=40, ids=[1 << 24])

@@ -12,6 +12,7 @@ import os
 import socket
 import subprocess
 import sys
+import types
 
 import pytest
 
@@ -175,3 +176,50 @@ def test_chain_sharded_ensemble_composes_like_one_rank():
         else:
             assert md == pytest.approx(r["max_delta"], rel=1e-9), it
     assert sum(not np.isnan(x[2]) for x in res[0]) == n_iter - ref.window_T + 1
+
+
+# ---- the batch split over ranks by problems (laps_batch_partition, host only)
+
+def _partition_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    from paper_2601_16696_gb300 import laps, workloads
+    laps.lib()  # host-only call: no GPU
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # batch64's shapes (no initial positions drawn): 64 small problems, then d = 10^4, M = 16384
+        probs = [types.SimpleNamespace(d=d, M=M) for d, _, M in workloads.batch64_shapes()]
+        probs.append(types.SimpleNamespace(d=10000, M=16384))
+        mine = laps.partition_problems(probs, world)[rank]
+        got = [None] * world
+        dist.all_gather_object(got, mine)
+        out.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partition_two_ranks_agree_and_cover_the_batch():
+    """Each of two gloo ranks computes its own share of the 65-problem batch;
+    the shares are disjoint, cover every problem once, and every rank sees
+    the same split."""
+    from paper_2601_16696_gb300 import build
+    build.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_partition_worker, args=(k, 2, port, q)) for k in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, g0), (_, g1) = res
+    assert g0 == g1
+    shares = g0
+    assert sorted(shares[0] + shares[1]) == list(range(65))
+    assert not set(shares[0]) & set(shares[1])
+    # the d = 10^4 problem (index 64, 70% of the coordinates) alone on one rank
+    big = [r for r in range(2) if 64 in shares[r]][0]
+    assert shares[big] == [64]
