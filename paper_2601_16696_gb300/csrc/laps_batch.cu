@@ -139,6 +139,12 @@ __device__ __forceinline__ ff gsum_ff(Grp& G, ff v) {
     return t;
 }
 
+// bytes (a multiple of 16) at a 16-byte aligned global address into L2
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------- maps on a group
 // App. E, Eq. "O update" (Z ~ N(0, I/d) per coordinate; c2s = c2 / sqrt(d))
 template <int CPL>
@@ -438,6 +444,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(const __grid_constant__ B
                 const int64_t mm = base + Gc.grp;
                 const bool act = mm < m1;
                 const uint32_t m = (uint32_t)mm;
+                // unadjusted phase: the next round's rows of y and u into L2 while this
+                // round's single step runs (one bulk prefetch per row from the group's
+                // first lane; a hint, no wait).  A MAMS round is long enough without it.
+                if (B.mode == 1 && sH.phase == 0 && Gc.gl == 0 && mm + ng < m1) {
+                    const size_t row = (size_t)(mm + ng) * P.d_pad;
+                    l2_prefetch(P.y + row, (uint32_t)P.d_pad * 4u);
+                    l2_prefetch(P.u + row, (uint32_t)P.d_pad * 4u);
+                }
                 float y[CPL], u[CPL];
                 auto load = [&](const float* src, float(&v)[CPL]) {
 #pragma unroll
