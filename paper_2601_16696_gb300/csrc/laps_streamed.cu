@@ -575,9 +575,13 @@ laps_status streamed_setup(laps_ctx* c) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
-    // one chain per warp: a chain update is a chain of dependent reductions and
-    // Philox rounds, so the kernel wants many chains in flight, not long loops
-    c->seg_G = (int)((c->M + kSegWarps - 1) / kSegWarps);
+    // A chain update is a chain of dependent reductions and Philox rounds, so the
+    // kernel wants many chains in flight; but every block's columns are one more
+    // partial for the finalise to add.  Up to four chains per warp, as long as
+    // every SM keeps a block (M = 8192: 256 blocks, 0.149 -> 0.143 ms per
+    // mixed-precision logistic-regression step against one chain per warp).
+    const int64_t g1 = (c->M + kSegWarps - 1) / kSegWarps, g4 = (c->M + 4 * kSegWarps - 1) / (4 * kSegWarps);
+    c->seg_G = (int)std::min<int64_t>(g1, std::max<int64_t>(g4, nsm));
     c->G = c->seg_G;
     c->seg_smem = (size_t)NQ * kSegWarps * dp * sizeof(float) + (size_t)kSegWarps * NCS * sizeof(ff);
     e = ensure_dyn_smem((const void*)seg_fn(c->seg_cpl), c->seg_smem);
