@@ -124,7 +124,10 @@ inline bool streamed_kind(int kind) { return kind == TGT_LOGREG || kind == TGT_G
 // the float-float partial the chain updates read (lp32: device [M] scratch)
 laps_status user_grad(const laps_target* tg, const float* W, int64_t M, int ld, float* G, float* lp32,
                       float2* LP, cudaStream_t st);
-laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
+// The data split of a contraction target's FP32 gradient (1 but for LOGREG), and
+// the gradient with it: gpart [S][M][kp], lpart [S][M], summed in order by the caller.
+int streamed_target_splits(const laps_target* tg, int64_t M);
+laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, int S, float* gpart,
                                  float2* lpart, cudaStream_t st);
 laps_status status_error(int device_status);
 void stats_from_hyper(const Hyper& h, laps_stats* out);

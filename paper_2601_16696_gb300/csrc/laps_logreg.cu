@@ -192,6 +192,46 @@ cudaError_t launch_f32(const LogregData& D, const float* W, int64_t M, int S, fl
 
 }  // namespace
 
+namespace {
+template <int KP>
+int f32_blocks_per_sm() {
+    int n = 0;
+    if (cudaFuncSetAttribute(logreg_grad_f32_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)f32_smem<KP>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, logreg_grad_f32_kernel<KP>, NT, f32_smem<KP>()) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    return std::max(n, 1);
+}
+}  // namespace
+
+int logreg_f32_splits(const LogregData& D, int64_t M, int nsm) {
+    int bps = 1;
+    switch (D.kp) {
+    case 64: bps = f32_blocks_per_sm<64>(); break;
+    case 128: bps = f32_blocks_per_sm<128>(); break;
+    case 192: bps = f32_blocks_per_sm<192>(); break;
+    case 256: bps = f32_blocks_per_sm<256>(); break;
+    }
+    const int64_t tiles = (M + TM - 1) / TM, slots = (int64_t)bps * std::max(nsm, 1);
+    const int chunks = std::max(1, (D.n + TN - 1) / TN);
+    // a block's time ~ its rows plus about one chunk of fixed work (the W tile in,
+    // the partials out); the run's time ~ waves x that
+    int best = 1;
+    int64_t best_cost = -1;
+    for (int S = 1; S <= std::min(16, chunks); ++S) {
+        const int64_t waves = (tiles * S + slots - 1) / slots;
+        const int64_t cost = waves * ((D.n + S - 1) / S + TN);
+        if (best_cost < 0 || cost < best_cost) {
+            best = S;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 cudaError_t logreg_grad_f32(const LogregData& D, const float* W, int64_t M, int S, float* gpart,
                             float2* lpart, cudaStream_t st, const int* guard) {
     if (M <= 0) return cudaSuccess;

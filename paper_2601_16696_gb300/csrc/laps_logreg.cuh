@@ -73,5 +73,9 @@ cudaError_t logreg_grad_x3(const LogregData& D, const float* W32, int64_t M, int
 // or a switch); the kernel then returns at once.
 cudaError_t logreg_grad_f32(const LogregData& D, const float* W, int64_t M, int S, float* gpart,
                             float2* lpart, cudaStream_t st, const int* guard = nullptr);
+// The data split S of logreg_grad_f32 for M points on nsm SMs: the number of row
+// ranges (1 .. 16) that minimises waves of blocks x rows per block, so that the
+// last wave of chain tiles x ranges fills the GPU (M = 8192 on 152 SMs: 7).
+int logreg_f32_splits(const LogregData& D, int64_t M, int nsm);
 
 }  // namespace laps

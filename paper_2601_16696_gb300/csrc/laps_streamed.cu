@@ -590,10 +590,9 @@ laps_status streamed_setup(laps_ctx* c) {
     c->smax = (c->d + c->fin_G - 1) / c->fin_G;
     c->fin_slice_smem = ((size_t)NQ * c->smax + NCS) * sizeof(ff);
     c->fin_gather_smem = (size_t)dp * sizeof(float);
-    // data splits of the gradient: about two blocks of 64 chains per SM
-    const int64_t tiles = (c->M + 63) / 64;
-    c->nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * nsm + tiles - 1) / tiles));
-    if (c->tg->kind != TGT_LOGREG) c->nsplit = 1;  // one evaluation writes every coordinate of its chains
+    // data splits of the FP32 gradient: whole waves of (chain tile, row range) blocks
+    c->nsplit = c->tg->kind == TGT_LOGREG ? logreg_f32_splits(c->tg->lr, c->M, nsm)
+                                          : 1;  // one evaluation writes every coordinate of its chains
     c->adj_integ = (c->d > c->cfg.mn4_min_dim) ? INTEG_MN4 : INTEG_MN2;
     coefs_table(c->cf);
     const int pr = (int)c->cfg.precision;
@@ -711,13 +710,21 @@ laps_status streamed_step(laps_ctx* c, int n_iters, cudaStream_t st) {
     return LAPS_OK;
 }
 
-laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, float* gpart,
+int streamed_target_splits(const laps_target* tg, int64_t M) {
+    if (tg->kind != TGT_LOGREG) return 1;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return logreg_f32_splits(tg->lr, M, nsm);
+}
+
+laps_status streamed_target_grad(const laps_target* tg, const float* W, int64_t M, int S, float* gpart,
                                  float2* lpart, cudaStream_t st) {
     if (tg->kind == TGT_GAUSS_DENSE) {
         cudaError_t e = gauss_dense_grad(tg->prec_dense, tg->d_pad, tg->d, W, M, gpart, lpart, st);
         return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "dense Gaussian gradient");
     }
-    cudaError_t e = logreg_grad_f32(tg->lr, W, M, 1, gpart, lpart, st);
+    cudaError_t e = logreg_grad_f32(tg->lr, W, M, S, gpart, lpart, st);
     return e == cudaSuccess ? LAPS_OK : cuda_fail(e, "logreg gradient");
 }
 

@@ -121,18 +121,19 @@ laps_status user_grad(const laps_target* tg, const float* W, int64_t M, int ld, 
 static laps_status streamed_logp_grad(const laps_target* tg, const float* x, int64_t M, float* logp,
                                       float* grad, cudaStream_t st) {
     const int kp = tg->d_pad, d = tg->d;
+    const int S = streamed_target_splits(tg, M);
     float *W = nullptr, *G = nullptr;
     float2* lp = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&W, (size_t)M * kp * 4, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G, (size_t)M * kp * 4, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&lp, (size_t)M * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G, (size_t)S * M * kp * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&lp, (size_t)S * M * 8, st);
     laps_status rs = LAPS_OK;
     if (e == cudaSuccess) {
         const int blocks = (int)std::min<int64_t>((M * kp + 255) / 256, 4096);
         logreg_pack_kernel<<<blocks, 256, 0, st>>>(x, W, M, d, kp);
-        rs = streamed_target_grad(tg, W, M, G, lp, st);
+        rs = streamed_target_grad(tg, W, M, S, G, lp, st);
         if (rs == LAPS_OK) {
-            logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp, 1);
+            logreg_unpack_kernel<<<blocks, 256, 0, st>>>(G, lp, grad, logp, M, d, kp, S);
             e = cudaGetLastError();
         }
     }

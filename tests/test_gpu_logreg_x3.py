@@ -85,7 +85,12 @@ def test_x3_logp_grad(L, ora, n, nf, M):
 
 def test_x3_logp_grad_full_size_sampled(L, ora):
     """The bench's logistic regression (n = 10^4, d = 101, M = 8192), one launch
-    over every chain; 64 sampled chains against the oracle."""
+    over every chain; 64 sampled chains against the oracle.  The split form's
+    gradient stays under the FP32 bar (1e-5 of max|g|), which the BF16 form
+    misses by far, so the bar tells the two classes apart.  At this size the
+    FP32 form adds its rows in seven ranges of ~1430 (the wave-filling split),
+    the split form in two ranges of 5000 in tensor memory, so here the FP32
+    form is the more accurate of the two (printed)."""
     pr = W.logreg(n_steps=10)
     assert pr.M == 8192 and pr.d == 101
     rng = np.random.default_rng(8)
@@ -99,8 +104,12 @@ def test_x3_logp_grad_full_size_sampled(L, ora):
     eg, el = _errs(g[idx], lp[idx], gr, lpr)
     lp32, g32 = tg.logp_grad(xd, precision=0)
     eg32, el32 = _errs(g32[idx], lp32[idx], gr, lpr)
+    lp16, g16 = tg.logp_grad(xd, precision=1)
+    eg16, _ = _errs(g16[idx], lp16[idx], gr, lpr)
+    print("full-size gradient error / max|g|: split form %.2e, FP32 form %.2e, BF16 form %.2e" % (eg, eg32, eg16))
     assert eg < 1e-5, (eg, eg32)
-    assert eg <= max(4.0 * eg32, 2e-6), (eg, eg32)
+    assert eg32 < 1e-5, eg32
+    assert eg16 > 1e-5, eg16
     assert el < 2e-6, (el, el32)
     assert torch.isfinite(g).all() and torch.isfinite(lp).all()
 
