@@ -20,7 +20,10 @@
  * closed forms on Gaussians; MAMS by a brute-force transition histogram and
  * stationarity; the full run by exact Gaussian / banana / funnel moments.
  * Logistic regression log p and gradient are pinned by finite differences and
- * by the closed form at w = 0; its sampled moments are parity unpinned.
+ * by the closed form at w = 0; a whole run on a two-dimensional posterior by
+ * the brute-force integral of its second moments (tests/test_oracle_runs.py).
+ * The full-size posterior's moments come from importance sampling with this
+ * log density, its estimator pinned by the same integral in 2-D.
  */
 #include "laps_oracle.h"
 

@@ -115,3 +115,24 @@ def test_step_count_and_stop(ora):
     assert len(adj) == (107 - 30) // 15
     assert run.t == 30 + 15 * len(adj) <= 107
     assert run.window_T == 22
+
+
+def test_logreg_2d_run_against_integration(ora):
+    """The oracle's whole run on a logistic-regression posterior (Sec. 6 target
+    stand-in) small enough to integrate: an intercept and one standardised
+    feature, n = 400 rows.  2048 chains, 300 unadjusted steps, then MAMS to step
+    1200; the final ensemble's E[w_i^2] against the brute-force integral of the
+    posterior on a grid: b^2 (Eq. "bias") below 10/M, where M exact samples give
+    about 1/M per coordinate."""
+    from test_workloads import _grid_moments
+    pr = W.logreg(n_data=400, n_feat=1, M=2048, n_steps=1200, data_seed=3)
+    ex2, var2, _, _ = _grid_moments(ora, pr)
+    ot = ora.OracleTarget(pr.kind, pr.d, X=pr.X, y=pr.y, prior_var=pr.prior_var)
+    run = ora.OracleLAPS(ot, pr.x0, seed=0, n_total_steps=pr.n_steps, force_switch_at=300)
+    run.run()
+    assert run.t_switch == 300
+    x = run.x()
+    b2 = ((x ** 2).mean(0) - ex2) ** 2 / var2
+    assert b2.max() < 10.0 / pr.M, (b2, ex2)
+    assert abs(run.trace[-1]["acc"] - 0.7) < 0.1
+
