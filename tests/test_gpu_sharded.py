@@ -117,12 +117,14 @@ def test_one_rank_equals_unsharded(L):
     assert a.stats()["t_switch"] == b.stats()["t_switch"] == 100
 
 
-def test_two_ranks_first_steps_match_oracle(L, ora):
+@pytest.mark.parametrize("n", [2, 3])
+def test_two_ranks_first_steps_match_oracle(L, ora, n):
     """Fixed step size: per-chain positions of the union within 1e-5 of the
-    unsharded run and of the oracle over 10 steps; both ranks' L equal."""
+    unsharded run and of the oracle over 10 steps; every rank's L equal (two
+    ranks of 150 and 151 chains, three of 100, 100 and 101)."""
     pr = W.logreg(n_data=1000, M=301, n_steps=200)
     cfg = dict(fixed_eps=0.01)
-    ranks, tg = _run_ranks(L, pr, 2, 3, 10, **cfg)
+    ranks, tg = _run_ranks(L, pr, n, 3, 10, **cfg)
     one = L.Sampler(tg, pr.M, n_total_steps=pr.n_steps, **cfg)
     one.init(torch.tensor(pr.x0, dtype=torch.float32, device="cuda"), seed=3)
     one.step(10)
@@ -132,8 +134,9 @@ def test_two_ranks_first_steps_match_oracle(L, ora):
     r = ora.OracleLAPS(ot, pr.x0, seed=3, n_total_steps=pr.n_steps, **cfg)
     r.iterate(10)
     assert _rel(xu, r.x()) <= 1e-5
-    la, lb = [q["L"] for q in ranks[0].trace()], [q["L"] for q in ranks[1].trace()]
-    assert la == lb
+    la = [q["L"] for q in ranks[0].trace()]
+    for k in range(1, n):
+        assert [q["L"] for q in ranks[k].trace()] == la
     for a, b in zip(la, r.trace):
         assert a == pytest.approx(b["L"], rel=1e-5)
 
