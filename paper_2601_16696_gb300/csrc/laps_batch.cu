@@ -189,11 +189,12 @@ __device__ __forceinline__ void g_blk(const Grp& G, const KParams& P, const floa
 }
 
 // ---------------------------------------------------------------- fused step
-// One step O_{eps/2} Phi_eps O_{eps/2} with three group reductions instead of
-// six: the first O map's |v|^2 is reduced together with g.v and |g|^2 (the
-// first B's g.u is (g.v)/|v|); each A map's log p change together with the
-// next B's |g'|^2 and g'.u; the last O map's |v|^2 together with the
-// non-finite flag of the chain update (when `check`).  Each map is App. E's:
+// One step O_{eps/2} Phi_eps O_{eps/2} with fewer group reductions than maps:
+// the first O map's |v|^2 is reduced together with g.v and |g|^2 (the first
+// B's g.u is (g.v)/|v|); each A map's reduction carries the next B's |g'|^2
+// and g'.u, while the A maps' log p changes stay per lane until the step's
+// (or the proposal's) end, where they are reduced with the last O map's |v|^2
+// and the non-finite flag of the chain update (`check`).  Each map is App. E's:
 // O as g_o, B in the overflow-free zeta = e^-delta form, A with the log p
 // change in difference form -1/2 prec (x' - x)(x' + x).
 
