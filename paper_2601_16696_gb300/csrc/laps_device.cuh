@@ -202,13 +202,18 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // 1.19 without; whole banana run 32.2 -> 31.1 ms).  The wait is bounded: after timeout_ns
 // the block records ST_TIMEOUT in *status and returns false, as does every
 // block that sees a recorded error, so the kernel always terminates.
-__device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, unsigned target,
-                                                long long timeout_ns) {
-    __shared__ int s_ok2;
+// The barrier comes in two halves, for a block that has work touching no other
+// block's data to do while the others arrive: grid_arrive (all threads), that
+// work, then grid_wait (all threads); grid_sync_count is the two back to back.
+__device__ __forceinline__ void grid_arrive(unsigned* count) {
     __syncthreads();
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+}
+__device__ __forceinline__ bool grid_wait(const unsigned* count, int* status, unsigned target,
+                                          long long timeout_ns) {
+    __shared__ int s_ok2;
     if (threadIdx.x == 0) {
         int ok = 1;
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
         if (ld_acquire_u32(count) < target) {
             const uint64_t t0 = global_ns();
             unsigned spins = 0;
@@ -228,6 +233,11 @@ __device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, un
     }
     __syncthreads();
     return s_ok2 != 0;
+}
+__device__ __forceinline__ bool grid_sync_count(unsigned* count, int* status, unsigned target,
+                                                long long timeout_ns) {
+    grid_arrive(count);
+    return grid_wait(count, status, target, timeout_ns);
 }
 
 }  // namespace laps

@@ -347,6 +347,12 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
 
     const int n_iter = (P.mode == 0) ? 1 : P.n_iters;
     unsigned n_bar = 0;  // grid barriers passed in this launch
+    // the O maps' noise of an unadjusted step depends only on its counters, so the
+    // next step's is drawn while this iteration's grid barriers are outstanding
+    // (z_o1 in the first, z_o2 in the second); z_t names the step it belongs to
+    float z_o1[CPL], z_o2[CPL];
+    bool z_pre = false;
+    uint32_t z_t = 0u;
 #ifdef LAPS_PHASE_TIMING
     unsigned long long phase_t_ = 0;
 #endif
@@ -372,12 +378,13 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             ff dl = ff_make(0.0f);
             if (H.phase == 0) {
                 const uint32_t t = (uint32_t)H.t;
-                float z1[CPL], z2[CPL];
-                o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O1, z1);
-                o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O2, z2);
-                o_apply<LPC, CPL>(P, gl, c1, c2s, z1, u);
+                if (!(z_pre && z_t == t)) {
+                    o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O1, z_o1);
+                    o_noise<LPC, CPL>(P, gl, active, m, t, TAG_O2, z_o2);
+                }
+                o_apply<LPC, CPL>(P, gl, c1, c2s, z_o1, u);
                 phi_step_k<KIND, LPC, CPL, 2>(P, CF, INTEG_LF, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
-                o_apply<LPC, CPL>(P, gl, c1, c2s, z2, u);
+                o_apply<LPC, CPL>(P, gl, c1, c2s, z_o2, u);
             } else {
                 // App. F step 2: u uniform on the sphere
                 const uint32_t pidx = (uint32_t)H.p;
@@ -530,16 +537,26 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         }
         LAPS_PHASE_MARK(3);
         // ------------------------------------------------ 3. barrier, then this block's slice
+        // an unadjusted iteration that is not the launch's last draws the next step's
+        // noise (step t + 1 if this iteration stays unadjusted) inside its barriers
+        // (not with the full-rank proxy or 16 coordinates per lane, whose kernels have
+        // no registers to spare)
+        const bool z_next = !FR && CPL <= 8 && P.mode == 1 && H.phase == 0 && it + 1 < n_iter;
+        const uint32_t t_next = (uint32_t)H.t + 1u;
         n_bar += 1;
-        if (!grid_sync_count(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns))
-            return;
+        grid_arrive(P.bar_count);
+        if (z_next) o_noise<LPC, CPL>(P, gl, active, m, t_next, TAG_O1, z_o1);
+        if (!grid_wait(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns)) return;
         LAPS_PHASE_MARK(4);
         ens_slice(P, H, s_q, blockIdx.x, G, FR ? s_fr : nullptr);
         LAPS_PHASE_MARK(5);
         // ------------------------------------------------ 4. barrier, then every block gathers
         n_bar += 1;
-        if (!grid_sync_count(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns))
-            return;
+        grid_arrive(P.bar_count);
+        if (z_next) o_noise<LPC, CPL>(P, gl, active, m, t_next, TAG_O2, z_o2);
+        if (!grid_wait(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns)) return;
+        z_pre = z_next;
+        z_t = t_next;
         LAPS_PHASE_MARK(6);
         ens_gather(P, H, s_var, FS);
         // the trace row (block 0), written by the last warp while the others go on
