@@ -353,6 +353,10 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
     float z_o1[CPL], z_o2[CPL];
     bool z_pre = false;
     uint32_t z_t = 0u;
+    // likewise a MAMS proposal's first step's O-map noise (z_o1, z_o2), drawn inside the
+    // previous proposal's barriers; a_t names the step it belongs to
+    bool a_pre = false;
+    uint32_t a_t = 0u;
 #ifdef LAPS_PHASE_TIMING
     unsigned long long phase_t_ = 0;
 #endif
@@ -388,6 +392,8 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
             } else {
                 // App. F step 2: u uniform on the sphere
                 const uint32_t pidx = (uint32_t)H.p;
+                const uint32_t t0 = (uint32_t)H.t;
+                const bool pre = a_pre && a_t == t0;
                 float n2 = 0.0f;
 #pragma unroll
                 for (int k = 0; k < NB; ++k) {
@@ -407,18 +413,18 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) u[q] *= inv;
                 // steps 3-4: N steps of phi with partial refreshes
-                const uint32_t t0 = (uint32_t)H.t;
                 for (int n = 0; n < P.N; ++n) {
-                    float z1[CPL], z2[CPL];
-                    o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O1, z1);
-                    o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O2, z2);
-                    o_apply<LPC, CPL>(P, gl, c1, c2s, z1, u);
+                    if (n > 0 || !pre) {
+                        o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O1, z_o1);
+                        o_noise<LPC, CPL>(P, gl, active, m, t0 + n, TAG_O2, z_o2);
+                    }
+                    o_apply<LPC, CPL>(P, gl, c1, c2s, z_o1, u);
                     if (H.integ == INTEG_MN2)
                         phi_step_k<KIND, LPC, CPL, 3>(P, CF, INTEG_MN2, eps, gl, lane, dsm, y, u, g, lp, dl, pr,
                                                       sg);
                     else
                         phi_step<KIND, LPC, CPL>(P, CF, H.integ, eps, gl, lane, dsm, y, u, g, lp, dl, pr, sg);
-                    o_apply<LPC, CPL>(P, gl, c1, c2s, z2, u);
+                    o_apply<LPC, CPL>(P, gl, c1, c2s, z_o2, u);
                 }
             }
             // non-finite check over the chain's group
@@ -543,9 +549,14 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         // no registers to spare)
         const bool z_next = !FR && CPL <= 8 && P.mode == 1 && H.phase == 0 && it + 1 < n_iter;
         const uint32_t t_next = (uint32_t)H.t + 1u;
+        // a proposal that is not the launch's last draws the next one's first step's O-map
+        // noise (step t + N) the same way
+        const bool a_next = !FR && CPL <= 8 && P.mode == 1 && H.phase == 1 && it + 1 < n_iter;
+        const uint32_t t0_next = (uint32_t)H.t + (uint32_t)P.N;
         n_bar += 1;
         grid_arrive(P.bar_count);
         if (z_next) o_noise<LPC, CPL>(P, gl, active, m, t_next, TAG_O1, z_o1);
+        if (a_next) o_noise<LPC, CPL>(P, gl, active, m, t0_next, TAG_O1, z_o1);
         if (!grid_wait(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns)) return;
         LAPS_PHASE_MARK(4);
         ens_slice(P, H, s_q, blockIdx.x, G, FR ? s_fr : nullptr);
@@ -554,9 +565,12 @@ __global__ void __launch_bounds__(kMaxThreads) laps_resident_kernel(const KParam
         n_bar += 1;
         grid_arrive(P.bar_count);
         if (z_next) o_noise<LPC, CPL>(P, gl, active, m, t_next, TAG_O2, z_o2);
+        if (a_next) o_noise<LPC, CPL>(P, gl, active, m, t0_next, TAG_O2, z_o2);
         if (!grid_wait(P.bar_count, P.status, n_bar * (unsigned)(G + P.bar_extra), P.timeout_ns)) return;
         z_pre = z_next;
         z_t = t_next;
+        a_pre = a_next;
+        a_t = t0_next;
         LAPS_PHASE_MARK(6);
         ens_gather(P, H, s_var, FS);
         // the trace row (block 0), written by the last warp while the others go on
