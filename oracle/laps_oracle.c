@@ -12,9 +12,10 @@
  * the result does not depend on the thread count.
  *
  * Pins (tests/test_oracle_*.py check each against something other than this
- * file): Philox by its statistics and, on a GPU, bit equality with cuRAND's
- * device Philox4x32-10 on 2^20 random (counter, key) pairs
- * (tests/test_gpu_philox_curand.py); O/A/B by unit norm, reversibility and an RK4 solution of the
+ * file): Philox by its statistics, by the generator's published known-answer
+ * vectors and, on a GPU, bit equality with cuRAND's device Philox4x32-10 on
+ * 2^20 random (counter, key) pairs (tests/test_gpu_philox_curand.py); O/A/B by
+ * unit norm, reversibility and an RK4 solution of the
  * velocity ODE; integrators by coefficient identities and their convergence
  * order; Delta by its vanishing at the integrator order; F and D~_diag by
  * closed forms on Gaussians; MAMS by a brute-force transition histogram and
